@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the disconnected-loop hot path on one GB300 (or N replicas).
+
+Workload (32^3 x 64, eps 0.4, kappa 0.1612, a*mu 0.0055, antiperiodic in t):
+the Truncated Solver Method with N_HP = 24 high-precision (CG residual 1e-10,
+FP32 Krylov vectors, FP64 reliable updates) and N_LP = 500 low-precision
+(residual 1e-2, FP16 Krylov vectors) solves of the even-odd twisted-mass
+operator, batched 16 right-hand sides per launch, each solution contracted
+into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
+(4 exact orders) local loops for all 16 Gamma, every t, |p|^2 <= 9.
+
+One step = one quarter of the TSM sweep (6 HP-LP pairs + 125 fresh LP solves
+with their contractions; 4 steps = the full N_HP = 24, N_LP = 500 sweep) on
+noise vectors the step has not used before.
+
+value = loop estimates per second at equal statistical error: the number of
+plain high-precision loop estimates (one per noise vector) that would give the
+TSM step's error on the isoscalar axial loop (the worse of the two
+observables), per second.  Variances come from the per-noise observables of
+all steps run.  The plain FP64 CG reference is reported beside it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 64)
+EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
+N_HP, N_LP, SLICES, BLOCK = 24, 500, 4, 16
+TOL_HP, TOL_LP = 1e-10, 1e-2
+P2MAX = 9
+LINK_SEED, NOISE_SEED = 1002, 2002
+WORKLOAD = "tsm_32x32x32x64"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler over the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _equal_error(obs_hp, obs_pair, obs_lp, n_hp, n_lp, t_step):
+    """Plain-HP-equivalent estimates per second for the two observables."""
+    out = {}
+    for name, k in (("sigma", 0), ("axial", 2)):
+        f_hp = obs_hp[:, k] + 1j * obs_hp[:, k + 1]
+        f_pr = obs_pair[:, k] + 1j * obs_pair[:, k + 1]
+        f_lp = obs_lp[:, k] + 1j * obs_lp[:, k + 1]
+        v_hp = np.var(f_hp, ddof=1)
+        v_d = np.var(f_hp - f_pr, ddof=1)
+        v_lp = np.var(f_lp, ddof=1)
+        e2 = v_d / n_hp + v_lp / n_lp
+        n_eq = v_hp / e2 if e2 > 0 else float("nan")
+        out[name] = {"v_hp": float(v_hp), "v_diff": float(v_d), "v_lp": float(v_lp), "err2_step": float(e2),
+                     "plain_equiv_per_step": float(n_eq), "per_s": float(n_eq / t_step),
+                     "r_c": float(np.real(np.corrcoef(np.real(f_hp), np.real(f_pr))[0, 1]))}
+    return out
+
+
+def _links():
+    import synth
+    return synth.gauge_links(DIMS, EPS, LINK_SEED)
+
+
+def run_ours(args, rank, world, device):
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+
+    torch.cuda.set_device(device)
+    links = _links()
+    n_hp_s, n_lp_s = N_HP // SLICES, N_LP // SLICES
+    stream = torch.cuda.current_stream()
+    ctx = dl.dl_create(DIMS, device, stream)
+    dl.dl_load_gauge(ctx, links, -1.0, 12, 8)
+    dl.dl_set_params(ctx, KAPPA, AMU)
+    npm = len(dl.dl_momenta(P2MAX))
+
+    def params(step):
+        return dl.dl_tsm_params(n_hp=n_hp_s, n_lp=n_lp_s, tol_hp=TOL_HP, tol_lp=TOL_LP, prec_hp_lo=dl.DL_F32,
+                                prec_lp_lo=dl.DL_F16, delta_hp=0.1, block=BLOCK,
+                                seed=NOISE_SEED + 1000003 * (step + 1) + 7919 * rank, p2max=P2MAX, with_deriv=0,
+                                hpe=1, max_iter=200000, chunk=32)
+
+    loops = np.zeros((3, DIMS[3], npm, 1, 4, 4), dtype=np.complex128)
+    obs = {"hp": [], "pair": [], "lp": []}
+    infos = []
+
+    def step(i, record):
+        ohp, opr, olp = np.zeros((n_hp_s, 4)), np.zeros((n_hp_s, 4)), np.zeros((n_lp_s, 4))
+        st, info = dl.dl_tsm_run(ctx, params(i), loops, ohp, opr, olp)
+        obs["hp"].append(ohp)
+        obs["pair"].append(opr)
+        obs["lp"].append(olp)
+        if record:
+            infos.append(info)
+        return st
+
+    for i in range(args.warmup):
+        step(-1 - i, False)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    dl.dl_profile(ctx, 1)
+    launches0 = dl.dl_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(device) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            step(i, True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        tdist.barrier()
+    launches = dl.dl_kernel_launches() - launches0
+    prof = dl.dl_profile(ctx, 0)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    t_step = ms / 1e3 / args.steps
+
+    # e2e: the same step through the C ABI from pinned host memory (gauge field
+    # uploaded every step, loops and observables copied back)
+    pinned = torch.from_numpy(links.view(np.float64)).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        dl.lib().dl_load_gauge(ctx, pinned.data_ptr(), 0, -1.0, 12, 8)
+        step(1000 + i, False)
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+
+    # plain FP64 CG reference: one right-hand side at a time, FP64 storage,
+    # no reliable updates; timed over a bounded number of iterations and scaled
+    # by the measured HP iteration count
+    ref = plain_fp64_reference(dl, ctx, device, infos, n_hp_s)
+    dl.dl_destroy(ctx)
+
+    ohp, opr, olp = (np.concatenate(obs[k]) for k in ("hp", "pair", "lp"))
+    eq = _equal_error(ohp, opr, olp, n_hp_s, n_lp_s, t_step)
+    value = min(eq["sigma"]["per_s"], eq["axial"]["per_s"]) * world
+    e2e_value = min(eq["sigma"]["plain_equiv_per_step"], eq["axial"]["plain_equiv_per_step"]) / e2e_t * world
+    roof = roofline(prof, t_step)
+    it_hp = sum(i.iters_hp for i in infos) / max(1, len(infos) * n_hp_s)
+    it_lp = sum(i.iters_lp for i in infos) / max(1, len(infos) * (n_hp_s + n_lp_s))
+    return dict(value=value, t_step=t_step, wall=wall, eq=eq, roof=roof, launches=launches, ref=ref, e2e=e2e_value,
+                e2e_t=e2e_t, clocks=clk.summary(), it_hp=it_hp, it_lp=it_lp,
+                sec_hp=sum(i.seconds_hp for i in infos) / len(infos),
+                sec_lp=sum(i.seconds_lp for i in infos) / len(infos),
+                sec_ct=sum(i.seconds_contract for i in infos) / len(infos),
+                bytes_h2d=links.nbytes, bytes_d2h=loops.nbytes + 8 * 4 * (2 * n_hp_s + n_lp_s))
+
+
+def plain_fp64_reference(dl, ctx, device, infos, n_hp_s):
+    import torch
+    n_it = 64
+    V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+    eta = torch.empty((1, V * 12), dtype=torch.complex128, device="cuda")
+    sol = torch.empty_like(eta)
+    dl.dl_noise_z4(ctx, 5, 0, 1, eta, dl.DL_C128)
+    prm = dl.dl_solve_params(tol=1e-30, max_iter=n_it, prec_hi=dl.DL_F64, prec_lo=dl.DL_F64, delta=0.0, flavour=1,
+                             chunk=n_it)
+    dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)  # warm (graph capture)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st = dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)
+    torch.cuda.synchronize()
+    t_iter = (time.perf_counter() - t0) / n_it
+    it_hp = sum(i.iters_hp for i in infos) / max(1, len(infos) * n_hp_s)
+    del eta, sol
+    return {"sec_per_iter": t_iter, "hp_iters": it_hp, "sec_per_estimate": t_iter * it_hp,
+            "estimates_per_s": 1.0 / (t_iter * it_hp) if it_hp > 0 else None,
+            "how": f"{n_it} CG iterations timed, scaled by the mean HP iteration count"}
+
+
+def roofline(prof, t_step):
+    """Dominant stencil launch: algorithmic bytes per launch / average duration."""
+    peaks, kind = _peaks()
+    V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+    Vh = V // 2
+    link_b = {0: 144, 1: 48, 2: 16}  # FP64 recon 18, FP32 recon 12, FP16 recon 8
+    sp_b = {0: 192, 1: 96, 2: 52}    # spinor bytes per site (FP16: 48 + 4-byte norm)
+    units = {0: 2, 1: 3, 2: 2, 3: 7}  # spinor streams per stage (in, aux, out, r, y, p ...)
+    best = None
+    for stage in range(4):
+        for prec in range(3):
+            n, ms, items = prof[stage, prec]
+            if n <= 0:
+                continue
+            cols = items / n / Vh
+            bytes_launch = 4 * V * link_b[prec] + units[stage] * Vh * cols * sp_b[prec]
+            avg = ms / n / 1e3
+            rec = {"stage": stage, "prec": ["f64", "f32", "f16"][prec], "launches_sampled": int(n),
+                   "avg_ms": avg * 1e3, "cols": cols, "bytes": bytes_launch, "gbs": bytes_launch / avg / 1e9,
+                   "total_ms": ms}
+            if best is None or ms > best["total_ms"]:
+                best = rec
+    if best is None:
+        return None
+    peak = peaks["hbm_gbs"]
+    return {"bound": "hbm", "achieved": round(best["gbs"], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(best["gbs"] / peak, 4), "traffic": None,
+            "kernel": f"dslash stage {best['stage']} ({best['prec']} Krylov, {best['cols']:.1f} columns)",
+            "bytes_per_launch": best["bytes"], "avg_launch_ms": round(best["avg_ms"], 4), "peak_kind": kind}
+
+
+def cpu_oracle_sample():
+    """The FP64 oracle on the host: one CG iteration (Mhat^dag Mhat + vector updates)
+    on the full 32^3 x 64 lattice; returns seconds per iteration and threads used."""
+    from oracle import operator as op
+    links = _links()
+    dims = DIMS
+    x = op.project(np.ones((DIMS[3], DIMS[2], DIMS[1], DIMS[0], 4, 3), dtype=np.complex128), dims, 0)
+    t0 = time.perf_counter()
+    q = op.mhat(links, x, KAPPA, AMU, 1, -1.0, dims)
+    ax = op.mhat_dag(links, q, KAPPA, AMU, 1, -1.0, dims)
+    a = np.vdot(x.ravel(), ax.ravel()).real
+    x = x + (1.0 / a) * ax
+    dt = time.perf_counter() - t0
+    return dt, 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, world)
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    r = run_ours(args, rank, world, local)
+    if rank != 0:
+        return
+    ro = r["roof"]
+    # CPU baseline: the oracle, bounded sample (one CG iteration at full size), scaled
+    t_cpu, cores = cpu_oracle_sample()
+    it_hp, it_lp = r["it_hp"], r["it_lp"]
+    n_hp_s, n_lp_s = N_HP // SLICES, N_LP // SLICES
+    cpu_step = t_cpu * (n_hp_s * (it_hp + it_lp) + n_lp_s * it_lp)
+    axial = r["eq"]["axial"]
+    cpu_val = min(r["eq"]["sigma"]["plain_equiv_per_step"], axial["plain_equiv_per_step"]) / cpu_step
+    line = {
+        "metric": "loop estimates/sec at 32^3x64 at equal error (TSM vs plain HP estimates); Dslash HBM GB/s",
+        "value": round(r["value"], 4),
+        "unit": "loop estimates/s (equal error)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(r["t_step"] * 1e3, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f16/f32 Krylov, f64 reliable updates and accumulation",
+        "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
+                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
+                   "step": "1/4 of the TSM sweep: 6 HP-LP pairs + 125 LP solves + contractions",
+                   "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": ro,
+        "cpu_baseline": {"value": round(cpu_val, 6), "unit": "loop estimates/s (equal error)", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"one FP64 oracle CG iteration on 32^3x64 ({t_cpu:.1f} s), scaled by the measured "
+                                   f"iteration counts (HP {it_hp:.0f}, LP {it_lp:.0f}); contractions excluded"},
+        "e2e": {"value": round(r["e2e"], 4), "unit": "loop estimates/s (equal error)",
+                "h2d_bytes_per_step": int(r["bytes_h2d"]), "d2h_bytes_per_step": int(r["bytes_d2h"])},
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+        "detail": {"equal_error": r["eq"], "iters_hp": it_hp, "iters_lp": it_lp, "sec_hp_per_step": r["sec_hp"],
+                   "sec_lp_per_step": r["sec_lp"], "sec_contract_per_step": r["sec_ct"],
+                   "plain_fp64_cg": r["ref"],
+                   "vs_plain_fp64_cg": (r["value"] / r["ref"]["estimates_per_s"]) if r["ref"]["estimates_per_s"] else None},
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args, world):
+    """The oracle as it stands on the host cores, same metric and config: each step
+    is a bounded sample (one oracle CG iteration at full size) scaled to a step."""
+    per = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample()
+    for _ in range(args.steps):
+        per.append(cpu_oracle_sample()[0])
+    t_it = float(np.median(per))
+    line = {"impl": "reference", "metric": "loop estimates/sec at 32^3x64 at equal error (TSM vs plain HP estimates); "
+                                           "Dslash HBM GB/s",
+            "value": None, "unit": "loop estimates/s (equal error)", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 1), "higher_is_better": True,
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": None,
+                             "sample": "one FP64 oracle CG iteration on 32^3x64 per step"},
+            "e2e": {"value": None, "unit": "loop estimates/s (equal error)", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

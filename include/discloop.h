@@ -1,0 +1,228 @@
+/*
+ * discloop.h -- C ABI of the GB300 (sm_103a) disconnected-quark-loop library.
+ *
+ * The calls follow the paper's statement of the workflow (Alexandrou et al.,
+ * "Evaluation of disconnected quark loops for hadron structure using GPUs",
+ * App. A "Interfaces and workflow"): load a gauge field, set kappa and a*mu,
+ * generate Z4 noise, invert the even-odd preconditioned twisted-mass operator,
+ * contract the solutions into local and one-derivative loops per time slice and
+ * momentum, and combine low- and high-precision solves with the Truncated
+ * Solver Method.
+ *
+ * Conventions shared by every call
+ *   - Lattice dims[4] = {X, Y, Z, T}; every extent even, X*Y*Z*T/2 < 2^31.
+ *   - Site order lex = x + X*(y + Y*(z + Z*t)); parity (x+y+z+t)&1, even = 0.
+ *   - Gauge field: complex128 [T][Z][Y][X][mu][3][3], mu = 0:x 1:y 2:z 3:t,
+ *     U_mu(x) row-major.  The time-boundary factor is applied by the kernels.
+ *   - "Natural" spinor fields: complex [n][T][Z][Y][X][4][3] (spin-major,
+ *     colour-minor), complex128 (DL_C128) or complex64 (DL_C64), in DEVICE
+ *     memory unless a call says otherwise.
+ *   - Chiral Euclidean gammas: gamma_k = [[0,-i s_k],[i s_k,0]] (k = x,y,z),
+ *     gamma_t = [[0,1],[1,0]], gamma_5 = diag(1,1,-1,-1).  Gamma_b for
+ *     b = 0..15 is g_x^b0 g_y^b1 g_z^b2 g_t^b3.
+ *   - Operator (kappa normalisation, App. A Eq. A.1):
+ *       M_f psi = (1 + 2 i kappa amu f gamma_5) psi
+ *                 - kappa sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)]
+ *     f = +1 (u) or -1 (d).  Physical units: M_phys = M / (2 kappa).
+ *   - All device work is ordered on the context's stream; the stream passed
+ *     to dl_create (or the legacy default stream if NULL) waits for it before
+ *     a call returns.  Calls on one context are not thread-safe.
+ *   - Negative status = error (message in dl_last_error); positive status =
+ *     a non-fatal outcome (outputs and stats are filled).  No exceptions cross
+ *     this boundary.
+ *   - Ownership: the caller owns every pointer it passes; the context owns the
+ *     gauge field copies and all workspaces and frees them in dl_destroy.
+ */
+#ifndef DISCLOOP_H
+#define DISCLOOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dl_ctx dl_ctx;
+
+typedef enum {
+  DL_OK = 0,
+  DL_ERR_ARG = -1,    /* invalid argument (sizes, enum values, NULL) */
+  DL_ERR_CUDA = -2,   /* a CUDA call failed; the message names it */
+  DL_ERR_OOM = -3,    /* device allocation failed */
+  DL_ERR_STATE = -4,  /* call out of order (e.g. no gauge field loaded) */
+  DL_NOT_CONVERGED = 1, /* a solve reached max_iter; last iterate returned */
+  DL_BREAKDOWN = 3      /* a CG scalar became zero, negative or non-finite */
+} dl_status;
+
+typedef enum { DL_F64 = 0, DL_F32 = 1, DL_F16 = 2 } dl_prec;     /* storage precision */
+typedef enum { DL_C128 = 0, DL_C64 = 1 } dl_dtype;              /* natural field element type */
+
+/* Operators applied by dl_apply (natural full-lattice fields in and out). */
+typedef enum {
+  DL_OP_M = 0,       /* out = M_f in                                       (Eq. A.1) */
+  DL_OP_MDAG = 1,    /* out = M_f^dagger in                                          */
+  DL_OP_HOP = 2,     /* out = D in (hopping sum, no kappa)                           */
+  DL_OP_MHAT = 3,    /* out_e = Mhat in_e, out_o = 0                        (Eq. A.2) */
+  DL_OP_MHAT_DAG = 4,/* out_e = Mhat^dagger in_e                                     */
+  DL_OP_PREP = 5,    /* out_e = in_e + kappa D_eo R_oo^-1 in_o (bhat of Eq. A.2)     */
+  DL_OP_RECON = 6,   /* out = in_e + R_oo^-1 (aux_o + kappa D_oe in_e)      (Eq. A.4) */
+  DL_OP_BH = 7       /* out = B H in, B = R_f^-1, H = -kappa D              (Eq. HPE) */
+} dl_op;
+
+/* Loop estimators (Sec. 2.3, 2.5). Output = factor * sum xi^dagger_a phi_b. */
+typedef enum {
+  DL_EST_STANDARD = 0, /* (eta, s)                 factor 1       -> Tr[M_u^-1 X]            (Eq. loopSt)  */
+  DL_EST_ONE_END = 1,  /* (g5 s, s)                factor -4i k amu -> Tr[(M_u^-1 - M_d^-1) X] (Eq. loopVv)  */
+  DL_EST_GEN = 2,      /* (g5 s, g5 (eta - 2i k amu g5 s)) factor 2 -> Tr[(M_u^-1 + M_d^-1) X] (Eq. loopStD) */
+  DL_EST_HPE = 3       /* (eta, (BH)^4 s)          factor 1       -> Tr[X (BH)^4 M_u^-1]     (Eq. loopHPE1) */
+} dl_estimator;
+
+#define DL_MAX_RHS 32   /* right-hand sides per block */
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context for one lattice on CUDA device `device`.  `cuda_stream`
+ * (a cudaStream_t, may be NULL) is the caller's stream that every call orders
+ * itself after and before returning.  Allocates nothing large. */
+dl_status dl_create(dl_ctx** ctx, const int dims[4], int device, void* cuda_stream);
+void dl_destroy(dl_ctx* ctx);
+const char* dl_last_error(const dl_ctx* ctx);
+dl_status dl_set_stream(dl_ctx* ctx, void* cuda_stream);
+
+/* Load the gauge field (App. A, "Twisted mass fermion operator": links stored
+ * with 18, 12 or 8 reals).  `links` is complex128 [T][Z][Y][X][4][3][3] in host
+ * memory (links_on_device = 0) or device memory (1).  t_boundary = -1
+ * (antiperiodic in time, the default reading) or +1.  recon_f32 in {18,12,8}
+ * and recon_f16 in {12,8} choose the compressed copies the FP32 and FP16
+ * operators read; the FP64 operator always reads all 18 reals.  The links must
+ * be SU(3) for recon 12/8. */
+dl_status dl_load_gauge(dl_ctx* ctx, const double* links, int links_on_device,
+                        double t_boundary, int recon_f32, int recon_f16);
+
+/* Set kappa and the twisted mass a*mu (App. A Eq. A.1). */
+dl_status dl_set_params(dl_ctx* ctx, double kappa, double amu);
+
+/* ---- noise (Sec. 2.1, Eqs. eq1/eq2) ------------------------------------- */
+
+/* Z2 x iZ2 noise (entries (+-1 +- i)/sqrt(2)), or {1,i,-1,-i} if quadrant != 0,
+ * for noise indices first_index .. first_index+n-1, written as a natural field
+ * `out` of type dtype.  Entry (r, lex, spin a, colour c) is bits 0 and 1 of
+ * splitmix64(seed, (r*V + lex)*12 + 3a + c), splitmix64 as published by Steele,
+ * Lea & Flood (2014): state = seed + (counter+1)*0x9E3779B97F4A7C15. */
+dl_status dl_noise_z4(dl_ctx* ctx, uint64_t seed, uint64_t first_index, int n,
+                      void* out, int dtype, int quadrant);
+
+/* ---- operators (App. A) -------------------------------------------------- */
+
+/* Apply `op` (dl_op) with flavour f (+1/-1) in storage precision `prec` to n
+ * natural fields `in` (and `aux` for DL_OP_RECON; else NULL), writing `out`.
+ * in/aux/out are device pointers of type dtype; out must not alias in. */
+dl_status dl_apply(dl_ctx* ctx, int op, int prec, int flavour, int n,
+                   const void* in, const void* aux, void* out, int dtype);
+
+/* ---- solver (Sec. 2.2) ---------------------------------------------------- */
+
+typedef struct {
+  double tol;       /* stop when |r| / |Mhat^dag bhat| < tol, r the CG residual (Sec. 2.2) */
+  int max_iter;     /* per right-hand side */
+  int prec_hi;      /* DL_F64 or DL_F32: solution accumulator, reliable-update residual */
+  int prec_lo;      /* DL_F64, DL_F32 or DL_F16: Krylov vectors and operator in the loop */
+  double delta;     /* reliable update when |r| < delta * max|r| since the last one; 0 = never */
+  int flavour;      /* +1 (u) or -1 (d) */
+  int chunk;        /* iterations per CUDA-graph launch between host checks (>= 1) */
+} dl_solve_params;
+
+typedef struct {
+  int iters[DL_MAX_RHS];          /* CG iterations per right-hand side */
+  double resid[DL_MAX_RHS];       /* final |r|/|Mhat^dag bhat| from the recomputed residual */
+  double true_resid[DL_MAX_RHS];  /* |b - M psi| / |b| on the full lattice, in FP64 */
+  int reliable_updates;           /* total over right-hand sides */
+  int max_iters;
+  double seconds;
+} dl_solve_stats;
+
+/* Solve M_f psi = b for n <= DL_MAX_RHS natural fields b (src) into sol, by CG
+ * on the normal equations of the even-odd system (App. A Eq. A.2) with
+ * per-right-hand-side convergence masks, then Eq. A.4 for the odd sites.
+ * stats may be NULL.  Returns DL_NOT_CONVERGED if any column hit max_iter. */
+dl_status dl_solve(dl_ctx* ctx, const void* src, void* sol, int n, int dtype,
+                   const dl_solve_params* params, dl_solve_stats* stats);
+
+/* ---- contractions (App. A, "Contraction kernels") ------------------------- */
+
+/* Number of momenta n with |n|^2 <= p2max, and (if list != NULL) the list as
+ * int[3*count] (nx, ny, nz), ordered nz, ny, nx outer to inner, ascending. */
+dl_status dl_momenta(int p2max, int* count, int* list);
+
+/* Loops of estimator `est` for n pairs (eta[i], sol[i]) (natural fields of
+ * type dtype, device), with momenta |n|^2 <= p2max and phases exp(-i p.x).
+ * out (device, complex128) is [n][T][Np][nd][4][4], nd = 1 (local) or 5 with
+ * with_deriv (local, then the symmetric covariant derivative in x, y, z, t):
+ *   out[..][a][b] = factor * sum_x exp(-i p.x) xi^dagger_a(x) phi_b(x)
+ * so that the loop of insertion X is sum_ab X_ab out[..][a][b] (colour traced).
+ * accumulate != 0 adds into out instead of overwriting it. */
+dl_status dl_contract(dl_ctx* ctx, int est, const void* eta, const void* sol, int n,
+                      int dtype, int with_deriv, int p2max, double* out, int accumulate);
+
+/* Exact part of the hopping-parameter expansion for local insertions (Eq. HPE:
+ * orders 0 and 2; orders 1 and 3 vanish on the diagonal): the per-site 4x4
+ * matrix C_ab (colour traced) with Tr_x[X (B - BHB + (BH)^2 B - (BH)^3 B)] =
+ * sum_ab X_ab C_ab, written to out16 (host, complex128 [4][4]). */
+dl_status dl_hpe_exact(dl_ctx* ctx, int flavour, double* out16);
+
+/* ---- truncated solver method (Sec. 2.2, Eq. estiTSM) --------------------- */
+
+typedef struct {
+  int n_hp, n_lp;        /* HP-LP pairs and fresh LP solves */
+  double tol_hp, tol_lp; /* CG residual bounds */
+  int prec_hp_lo;        /* Krylov storage of HP solves (FP64 accumulation, reliable updates) */
+  int prec_lp_lo;        /* Krylov storage of LP solves (FP32 accumulation) */
+  double delta_hp;       /* reliable-update trigger for HP solves */
+  int block;             /* right-hand sides per batched solve, <= DL_MAX_RHS */
+  uint64_t seed;         /* noise seed; HP pairs use indices 0..n_hp-1, LP n_hp.. */
+  int p2max;             /* momentum cut */
+  int with_deriv;        /* add the one-derivative loops */
+  int hpe;               /* add the HPE standard-estimator loops */
+  int max_iter;
+  int chunk;
+} dl_tsm_params;
+
+typedef struct {
+  int np, nd, n_est;     /* momenta, derivative slots, estimators (ONE_END, GEN, [HPE]) */
+  double seconds_total, seconds_hp, seconds_lp, seconds_contract;
+  long long iters_hp, iters_lp; /* summed over right-hand sides */
+  int not_converged;     /* right-hand sides that hit max_iter */
+} dl_tsm_info;
+
+/* Run the TSM for one gauge field: n_hp HP/LP pairs and n_lp fresh LP solves,
+ * each followed by its contractions (one-end, generalised one-end, and the HPE
+ * standard estimator with its exact part added), noise generated on the
+ * device and never stored beyond a block.  Outputs (host memory, may be NULL):
+ *   loops  complex128 [n_est][T][Np][nd][4][4]: Eq. estiTSM per element;
+ *   obs_hp, obs_lp_pair  double [n_hp][4], obs_lp double [n_lp][4]: per-noise
+ *          scalar observables (sigma loop Re, Im; isoscalar axial loop Re, Im;
+ *          zero momentum, summed over t) for error estimates. */
+dl_status dl_tsm_run(dl_ctx* ctx, const dl_tsm_params* params, double* loops,
+                     double* obs_hp, double* obs_lp_pair, double* obs_lp, dl_tsm_info* info);
+
+/* ---- instrumentation ------------------------------------------------------ */
+
+/* Live timing of the stencil kernels inside the solver's CUDA graphs.  With
+ * profiling on, every captured chunk of CG iterations records CUDA events
+ * around the four operator launches of its first iteration (on the context's
+ * stream); durations are summed per stage and Krylov precision.  out (host,
+ * may be NULL) receives double[4 stages][3 precisions][3] = (launches sampled,
+ * milliseconds, site-column items processed) accumulated since the last reset.
+ * Stages: 0 = R^-1 D_oe, 1 = R - kappa^2 D_eo (+|q|^2), 2 = daggered stage 0,
+ * 3 = daggered stage 1 fused with the CG update.  enable = 1/0 switches
+ * profiling on/off and resets the sums; enable = -1 only reads them. */
+dl_status dl_profile(dl_ctx* ctx, int enable, double* out);
+
+/* Number of kernels this library has launched in the process so far (direct
+ * launches plus the kernel nodes of every CUDA-graph launch).  Thread-safe. */
+long long dl_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DISCLOOP_H */

@@ -1,0 +1,207 @@
+"""ctypes binding of libdiscloop.so: same names as the C ABI (include/discloop.h),
+argument marshalling only.  Device buffers are passed as torch tensors (their
+data_ptr) or raw integer addresses; host buffers as numpy arrays.  Negative
+status codes raise DLError; non-fatal positive codes are returned."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdiscloop.so")
+
+DL_OK, DL_ERR_ARG, DL_ERR_CUDA, DL_ERR_OOM, DL_ERR_STATE = 0, -1, -2, -3, -4
+DL_NOT_CONVERGED, DL_BREAKDOWN = 1, 3
+DL_F64, DL_F32, DL_F16 = 0, 1, 2
+DL_C128, DL_C64 = 0, 1
+(DL_OP_M, DL_OP_MDAG, DL_OP_HOP, DL_OP_MHAT, DL_OP_MHAT_DAG, DL_OP_PREP, DL_OP_RECON, DL_OP_BH) = range(8)
+DL_EST_STANDARD, DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE = range(4)
+DL_MAX_RHS = 32
+
+
+class DLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"discloop status {status}: {msg}")
+        self.status = status
+
+
+class dl_solve_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("prec_hi", C.c_int), ("prec_lo", C.c_int),
+                ("delta", C.c_double), ("flavour", C.c_int), ("chunk", C.c_int)]
+
+
+class dl_solve_stats(C.Structure):
+    _fields_ = [("iters", C.c_int * DL_MAX_RHS), ("resid", C.c_double * DL_MAX_RHS),
+                ("true_resid", C.c_double * DL_MAX_RHS), ("reliable_updates", C.c_int), ("max_iters", C.c_int),
+                ("seconds", C.c_double)]
+
+
+class dl_tsm_params(C.Structure):
+    _fields_ = [("n_hp", C.c_int), ("n_lp", C.c_int), ("tol_hp", C.c_double), ("tol_lp", C.c_double),
+                ("prec_hp_lo", C.c_int), ("prec_lp_lo", C.c_int), ("delta_hp", C.c_double), ("block", C.c_int),
+                ("seed", C.c_uint64), ("p2max", C.c_int), ("with_deriv", C.c_int), ("hpe", C.c_int),
+                ("max_iter", C.c_int), ("chunk", C.c_int)]
+
+
+class dl_tsm_info(C.Structure):
+    _fields_ = [("np", C.c_int), ("nd", C.c_int), ("n_est", C.c_int), ("seconds_total", C.c_double),
+                ("seconds_hp", C.c_double), ("seconds_lp", C.c_double), ("seconds_contract", C.c_double),
+                ("iters_hp", C.c_longlong), ("iters_lp", C.c_longlong), ("not_converged", C.c_int)]
+
+
+_lib = None
+
+# name -> (restype, argtypes); mirrors include/discloop.h
+_SIGS = {
+    "dl_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+    "dl_destroy": (None, [C.c_void_p]),
+    "dl_last_error": (C.c_char_p, [C.c_void_p]),
+    "dl_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dl_load_gauge": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]),
+    "dl_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    "dl_noise_z4": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "dl_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "dl_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(dl_solve_params),
+                           C.POINTER(dl_solve_stats)]),
+    "dl_momenta": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+    "dl_contract": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                              C.c_void_p, C.c_int]),
+    "dl_hpe_exact": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dl_kernel_launches": (C.c_longlong, []),
+    "dl_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "dl_tsm_run": (C.c_int, [C.c_void_p, C.POINTER(dl_tsm_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.POINTER(dl_tsm_info)]),
+}
+
+
+def lib():
+    """Load libdiscloop.so (built in-tree by paper_1309_2256_gb300.build); fail loudly if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_1309_2256_gb300.build.build() first "
+                              "(there is no fallback implementation)")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(ctx, status):
+    if status < 0:
+        msg = lib().dl_last_error(ctx).decode() if ctx else "(no context)"
+        raise DLError(status, msg)
+    return status
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def dl_create(dims, device=0, stream=None):
+    h = C.c_void_p()
+    d = (C.c_int * 4)(*dims)
+    st = lib().dl_create(C.byref(h), d, int(device), _stream_ptr(stream))
+    if st < 0:
+        raise DLError(st, "dl_create failed (dims must be even and >= 2; CUDA device must exist)")
+    return h.value
+
+
+def dl_destroy(ctx):
+    lib().dl_destroy(ctx)
+
+
+def dl_last_error(ctx):
+    return lib().dl_last_error(ctx).decode()
+
+
+def dl_set_stream(ctx, stream):
+    return _check(ctx, lib().dl_set_stream(ctx, _stream_ptr(stream)))
+
+
+def dl_load_gauge(ctx, links, t_boundary=-1.0, recon_f32=12, recon_f16=8):
+    """links: numpy complex128 [T][Z][Y][X][4][3][3] (host) or a CUDA complex128 tensor."""
+    on_dev = 0 if isinstance(links, np.ndarray) else 1
+    if on_dev == 0:
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+    return _check(ctx, lib().dl_load_gauge(ctx, _ptr(links), on_dev, float(t_boundary), int(recon_f32), int(recon_f16)))
+
+
+def dl_set_params(ctx, kappa, amu):
+    return _check(ctx, lib().dl_set_params(ctx, float(kappa), float(amu)))
+
+
+def dl_noise_z4(ctx, seed, first_index, n, out, dtype=DL_C128, quadrant=0):
+    return _check(ctx, lib().dl_noise_z4(ctx, int(seed), int(first_index), int(n), _ptr(out), int(dtype), int(quadrant)))
+
+
+def dl_apply(ctx, op, prec, flavour, n, inp, aux, out, dtype=DL_C128):
+    return _check(ctx, lib().dl_apply(ctx, int(op), int(prec), int(flavour), int(n), _ptr(inp), _ptr(aux), _ptr(out),
+                                      int(dtype)))
+
+
+def dl_solve(ctx, src, sol, n, dtype, params: dl_solve_params, stats: dl_solve_stats | None = None):
+    stats = stats if stats is not None else dl_solve_stats()
+    st = _check(ctx, lib().dl_solve(ctx, _ptr(src), _ptr(sol), int(n), int(dtype), C.byref(params), C.byref(stats)))
+    return st, stats
+
+
+def dl_momenta(p2max):
+    cnt = C.c_int()
+    st = lib().dl_momenta(int(p2max), C.byref(cnt), None)
+    if st < 0:
+        raise DLError(st, "dl_momenta: bad p2max")
+    lst = np.zeros(3 * cnt.value, dtype=np.int32)
+    lib().dl_momenta(int(p2max), C.byref(cnt), lst.ctypes.data)
+    return lst.reshape(-1, 3)
+
+
+def dl_contract(ctx, est, eta, sol, n, dtype, with_deriv, p2max, out, accumulate=0):
+    return _check(ctx, lib().dl_contract(ctx, int(est), _ptr(eta), _ptr(sol), int(n), int(dtype), int(with_deriv),
+                                         int(p2max), _ptr(out), int(accumulate)))
+
+
+def dl_hpe_exact(ctx, flavour=1):
+    out = np.zeros((4, 4), dtype=np.complex128)
+    _check(ctx, lib().dl_hpe_exact(ctx, int(flavour), out.ctypes.data))
+    return out
+
+
+def dl_tsm_run(ctx, params: dl_tsm_params, loops=None, obs_hp=None, obs_lp_pair=None, obs_lp=None):
+    info = dl_tsm_info()
+    st = _check(ctx, lib().dl_tsm_run(ctx, C.byref(params), _ptr(loops), _ptr(obs_hp), _ptr(obs_lp_pair), _ptr(obs_lp),
+                                      C.byref(info)))
+    return st, info
+
+
+def dl_profile(ctx, enable=-1):
+    """Returns float64 [4 stages][3 precisions][3] = (launches sampled, ms, items)."""
+    out = np.zeros((4, 3, 3), dtype=np.float64)
+    _check(ctx, lib().dl_profile(ctx, int(enable), out.ctypes.data))
+    return out
+
+
+def dl_kernel_launches():
+    return int(lib().dl_kernel_launches())

@@ -1,0 +1,1239 @@
+// C ABI of the discloop library: context, gauge loading, noise, operators,
+// the batched mixed-precision CG with reliable updates, contractions and the
+// Truncated Solver Method driver.  Every arithmetic step runs in the kernels of
+// dl_dslash.cu, dl_blas.cu, dl_layout.cu and dl_contract.cu; this file only
+// orders launches, owns device memory and reads back per-column scalars.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "discloop.h"
+#include "dl_kernels.h"
+
+#include <atomic>
+
+static std::atomic<long long> g_launches{0};
+void dl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+struct Field {
+  int prec = -1;
+  size_t items = 0;
+  void* data = nullptr;
+  float* norm = nullptr;
+  FieldRef ref() const { return FieldRef{data, norm}; }
+};
+
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernel nodes in the graph
+};
+
+int ilog2ceil(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+size_t chunk_bytes(int prec) { return prec == P64 ? 192 : (prec == P32 ? 96 : 48); }
+
+}  // namespace
+
+struct dl_ctx {
+  int dev = 0;
+  cudaStream_t st = nullptr;    // internal stream (non-blocking; capturable)
+  cudaStream_t user = nullptr;  // caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int dims[4] = {0, 0, 0, 0};
+  int Vh = 0;
+  double kappa = 0.125, amu = 0.0, tbc = -1.0;
+  int rec32 = 12, rec16 = 8;
+  void* g64 = nullptr;
+  void* g32 = nullptr;
+  void* g16 = nullptr;
+  bool has_gauge = false;
+  std::string err;
+  std::map<std::string, Field> ws;
+  double* partial = nullptr;
+  size_t partial_blocks = 0;
+  double* S = nullptr;  // [DL_NS][DL_NCMAX]
+  int* active = nullptr;
+  int* flags = nullptr;
+  int* iters = nullptr;
+  int* upd = nullptr;
+  int* all = nullptr;  // all-ones mask
+  double2* misc = nullptr;  // small complex scratch (HPE exact part, observables)
+  int* mom = nullptr;
+  int mom_p2 = -1, np = 0;
+  void* scratch = nullptr;  // contraction scratch
+  size_t scratch_bytes = 0;
+  std::map<std::string, DevBuf> bufs;
+  std::vector<GraphEntry> graphs;
+  // live stencil timing: events around the four operator launches of the first
+  // CG iteration of every captured chunk; sums per (stage, precision)
+  int profiling = 0;
+  cudaEvent_t pev[8] = {nullptr};
+  double prof_ms[4][3] = {{0}};
+  long long prof_n[4][3] = {{0}};
+  long long prof_items[4][3] = {{0}};  // site-column items processed, summed over sampled launches
+};
+
+namespace {
+
+dl_status fail(dl_ctx* c, dl_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (c) c->err = m;
+  return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
+}
+
+#define CK(expr)                                                   \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);         \
+  } while (0)
+
+Batch make_batch(const dl_ctx* c, int ncol) {
+  Batch B;
+  memset(&B, 0, sizeof(B));
+  B.nlat = 1;
+  LatDesc& L = B.lat[0];
+  L.X = c->dims[0];
+  L.Y = c->dims[1];
+  L.Z = c->dims[2];
+  L.T = c->dims[3];
+  L.Vh = c->Vh;
+  L.lognpad = ilog2ceil(std::max(ncol, 1));
+  L.ncol = ncol;
+  L.rhs_base = 0;
+  L.item_off = 0;
+  L.gsite_off = 0;
+  L.tbc = c->tbc;
+  L.kappa = c->kappa;
+  L.amu = c->amu;
+  dl::blocks_for(B, 256);
+  return B;
+}
+
+// Twist T = a + i b gamma_5 for R_f (inv = false) or R_f^{-1} (inv = true).
+void twist_ab(const dl_ctx* c, int f, bool inv, double& a, double& b) {
+  double w = 2.0 * c->kappa * c->amu * f;
+  if (!inv) {
+    a = 1.0;
+    b = w;
+  } else {
+    a = 1.0 / (1.0 + w * w);
+    b = -w / (1.0 + w * w);
+  }
+}
+
+// kinds of site factor: 0 identity, 1 R_f, 2 R_f^{-1}
+EpiSet epi(const dl_ctx* c, double coef, int t1, int f1, int t2, int f2) {
+  EpiSet E;
+  memset(&E, 0, sizeof(E));
+  Epi& e = E.e[0];
+  e.c = coef;
+  e.a1 = 1.0;
+  e.b1 = 0.0;
+  e.a2 = 1.0;
+  e.b2 = 0.0;
+  if (t1) twist_ab(c, f1, t1 == 2, e.a1, e.b1);
+  if (t2) twist_ab(c, f2, t2 == 2, e.a2, e.b2);
+  return E;
+}
+
+int grec_of(const dl_ctx* c, int prec) { return prec == P64 ? 18 : (prec == P32 ? c->rec32 : c->rec16); }
+
+void invalidate_graphs(dl_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+dl_status ensure_field(dl_ctx* c, const std::string& base, int prec, int ncol, Field** out) {
+  size_t items = (size_t)c->Vh << ilog2ceil(std::max(ncol, 1));
+  const std::string name = base + "#" + std::to_string(prec);
+  auto it = c->ws.find(name);
+  if (it != c->ws.end() && it->second.prec == prec && it->second.items >= items) {
+    *out = &it->second;
+    return DL_OK;
+  }
+  if (it != c->ws.end()) {
+    cudaFree(it->second.data);
+    if (it->second.norm) cudaFree(it->second.norm);
+    c->ws.erase(it);
+    invalidate_graphs(c);
+  }
+  Field f;
+  f.prec = prec;
+  f.items = items;
+  CK(cudaMalloc(&f.data, items * chunk_bytes(prec)));
+  if (prec == P16) CK(cudaMalloc((void**)&f.norm, items * sizeof(float)));
+  c->ws[name] = f;
+  *out = &c->ws[name];
+  return DL_OK;
+}
+
+dl_status ensure_partial(dl_ctx* c, const Batch& B) {
+  size_t nb = (size_t)B.blk_begin[B.nlat];
+  if (nb <= c->partial_blocks) return DL_OK;
+  if (c->partial) cudaFree(c->partial);
+  c->partial = nullptr;
+  CK(cudaMalloc((void**)&c->partial, std::max<size_t>(nb, 1) * DL_MAXC * sizeof(double)));
+  c->partial_blocks = nb;
+  invalidate_graphs(c);
+  return DL_OK;
+}
+
+dl_status ensure_scratch(dl_ctx* c, size_t bytes) {
+  if (bytes <= c->scratch_bytes) return DL_OK;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  CK(cudaMalloc(&c->scratch, bytes));
+  c->scratch_bytes = bytes;
+  return DL_OK;
+}
+
+dl_status ensure_buf(dl_ctx* c, const std::string& name, size_t bytes, void** out) {
+  auto it = c->bufs.find(name);
+  if (it != c->bufs.end() && it->second.bytes >= bytes) {
+    *out = it->second.p;
+    return DL_OK;
+  }
+  if (it != c->bufs.end()) {
+    cudaFree(it->second.p);
+    c->bufs.erase(it);
+  }
+  DevBuf b;
+  CK(cudaMalloc(&b.p, std::max<size_t>(bytes, 16)));
+  b.bytes = bytes;
+  c->bufs[name] = b;
+  *out = b.p;
+  return DL_OK;
+}
+
+// entry/exit ordering against the caller's stream
+dl_status enter(dl_ctx* c) {
+  CK(cudaSetDevice(c->dev));
+  CK(cudaEventRecord(c->ev_in, c->user));
+  CK(cudaStreamWaitEvent(c->st, c->ev_in, 0));
+  return DL_OK;
+}
+dl_status leave(dl_ctx* c) {
+  CK(cudaEventRecord(c->ev_out, c->st));
+  CK(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+  return DL_OK;
+}
+
+const FieldRef NOF = {nullptr, nullptr};
+
+// ---- operator stages (even-odd, App. A Eq. A.2) ----------------------------
+// out_o = R_{f'}^{-1} D^{(dag)}_oe in_e,  f' = dag ? -f : f
+cudaError_t stage1(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRef in_e, FieldRef out_o, const int* mask) {
+  int ff = dag ? -f : f;
+  EpiSet E = epi(c, 1.0, 2, ff, 0, 0);
+  GaugeSet g{c->g64, c->g32, c->g16};
+  return dl::dslash(B, prec, grec_of(c, prec), EPI_PLAIN, dag, 1, in_e, NOF, out_o, g, E, mask, nullptr, NOF, NOF, NOF,
+                    nullptr, c->st);
+}
+// out_e = R_{f'} aux_e - kappa^2 D^{(dag)}_eo in_o  (optionally |out|^2 partials)
+cudaError_t stage2(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRef in_o, FieldRef aux_e, FieldRef out_e,
+                   const int* mask, double* partial) {
+  int ff = dag ? -f : f;
+  EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, ff);
+  GaugeSet g{c->g64, c->g32, c->g16};
+  return dl::dslash(B, prec, grec_of(c, prec), partial ? EPI_AUX_NORM : EPI_AUX, dag, 0, in_o, aux_e, out_e, g, E, mask,
+                    partial, NOF, NOF, NOF, nullptr, c->st);
+}
+
+// Ax = Mhat^dag Mhat x (all in one precision), using two temporaries
+cudaError_t normal_op(dl_ctx* c, const Batch& B, int prec, int f, FieldRef x, FieldRef t_o, FieldRef q_e, FieldRef t2_o,
+                      FieldRef ax, const int* mask) {
+  DL_CUDA_TRY(stage1(c, B, prec, false, f, x, t_o, mask));
+  DL_CUDA_TRY(stage2(c, B, prec, false, f, t_o, x, q_e, mask, nullptr));
+  DL_CUDA_TRY(stage1(c, B, prec, true, f, q_e, t2_o, mask));
+  return stage2(c, B, prec, true, f, t2_o, q_e, ax, mask, nullptr);
+}
+
+// per-column sums of the partial buffer into S[slot]
+cudaError_t colsum(dl_ctx* c, const Batch& B, int slot) {
+  return dl::sum_partials(B, c->partial, c->S, DL_NCMAX, slot, B.lat[0].ncol, c->st);
+}
+
+// ---- the CG on the normal equations ----------------------------------------
+struct CGState {
+  std::vector<double> S;
+  std::vector<int> active, flags, iters;
+};
+
+dl_status download_state(dl_ctx* c, int n, CGState& h) {
+  h.S.resize(DL_NS * DL_NCMAX);
+  h.active.resize(n);
+  h.flags.resize(n);
+  h.iters.resize(n);
+  CK(cudaMemcpyAsync(h.S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(h.active.data(), c->active, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(h.flags.data(), c->flags, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(h.iters.data(), c->iters, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DL_OK;
+}
+
+dl_status upload_state(dl_ctx* c, int n, const CGState& h) {
+  CK(cudaMemcpyAsync(c->S, h.S.data(), sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->active, h.active.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->flags, h.flags.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return DL_OK;
+}
+
+struct CGFields {
+  Field *r, *p, *y, *t1, *q, *t2;      // low precision
+  Field *rh, *ax, *th1, *tq, *th2;     // high precision temporaries
+};
+
+// One CG iteration for all active columns (low precision); graph-capturable.
+cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta,
+                         bool timed = false) {
+  const int n = B.lat[0].ncol;
+  auto ev = [&](int k) { return timed ? cudaEventRecord(c->pev[k], c->st) : cudaSuccess; };
+  DL_CUDA_TRY(ev(0));
+  DL_CUDA_TRY(stage1(c, B, lo, false, f, F.p->ref(), F.t1->ref(), c->active));
+  DL_CUDA_TRY(ev(1));
+  DL_CUDA_TRY(ev(2));
+  DL_CUDA_TRY(stage2(c, B, lo, false, f, F.t1->ref(), F.p->ref(), F.q->ref(), c->active, c->partial));
+  DL_CUDA_TRY(ev(3));
+  DL_CUDA_TRY(colsum(c, B, DL_S_PAP));
+  DL_CUDA_TRY(dl::cg_alpha(n, c->S, c->active, c->flags, c->st));
+  DL_CUDA_TRY(ev(4));
+  DL_CUDA_TRY(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), c->active));
+  DL_CUDA_TRY(ev(5));
+  {
+    EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, -f);
+    GaugeSet g{c->g64, c->g32, c->g16};
+    DL_CUDA_TRY(ev(6));
+    DL_CUDA_TRY(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, c->active,
+                           c->partial, F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
+    DL_CUDA_TRY(ev(7));
+  }
+  DL_CUDA_TRY(colsum(c, B, DL_S_RRNEW));
+  DL_CUDA_TRY(dl::cg_beta(n, c->S, c->active, c->flags, c->iters, tol2, delta, c->st));
+  return dl::xpay(B, lo, F.p->ref(), F.r->ref(), c->S + DL_S_BETA * DL_NCMAX, c->active, c->st);
+}
+
+// Reliable update for the columns in `mask` (host vector): x += y, y = 0,
+// r_hi = b - A x (high precision), r = r_hi.  Returns |r_hi|^2 per column.
+dl_status reliable_update(dl_ctx* c, const Batch& B, int hi, int lo, int f, const CGFields& F, Field* x, Field* b,
+                          const std::vector<int>& mask, std::vector<double>& rr_true) {
+  const int n = B.lat[0].ncol;
+  CK(cudaMemcpyAsync(c->upd, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  CK(dl::accum(B, hi, lo, x->ref(), F.y->ref(), c->upd, 1, c->st));
+  CK(normal_op(c, B, hi, f, x->ref(), F.th1->ref(), F.tq->ref(), F.th2->ref(), F.ax->ref(), c->upd));
+  CK(dl::xmy_norm(B, hi, F.rh->ref(), b->ref(), F.ax->ref(), c->upd, c->partial, c->st));
+  CK(colsum(c, B, DL_S_TMP));
+  CK(dl::copy(B, lo, hi, F.r->ref(), F.rh->ref(), c->upd, c->st));
+  std::vector<double> S(DL_NS * DL_NCMAX);
+  CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  rr_true.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) rr_true[i] = S[DL_S_TMP * DL_NCMAX + i];
+  return DL_OK;
+}
+
+std::string graph_key(const dl_ctx* c, int lo, int f, int n, int chunk, double tol2, double delta, const CGFields& F) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d", lo, f, n, chunk, tol2,
+           delta, c->kappa, c->amu, F.r->data, F.p->data, F.y->data, F.t1->data, F.q->data, F.t2->data,
+           (void*)c->partial, c->rec32, c->rec16, c->profiling);
+  return std::string(buf);
+}
+
+dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, int chunk, double tol2, double delta,
+                    cudaGraphExec_t* out) {
+  std::string key = graph_key(c, lo, f, B.lat[0].ncol, chunk, tol2, delta, F);
+  for (auto& g : c->graphs)
+    if (g.key == key) {
+      *out = g.exec;
+      return DL_OK;
+    }
+  if (c->profiling && c->graphs.size() >= 4) invalidate_graphs(c);
+  cudaGraph_t graph;
+  const long long before = g_launches.load();
+  CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = cg_iteration(c, B, lo, f, F, tol2, delta, c->profiling && k == 0);
+  cudaError_t e2 = cudaStreamEndCapture(c->st, &graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capture of the CG iteration");
+  CK(e2);
+  cudaGraphExec_t exec;
+  CK(cudaGraphInstantiate(&exec, graph, 0));
+  cudaGraphDestroy(graph);
+  if (c->graphs.size() >= 4) {
+    cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  const long long nodes = g_launches.load() - before;
+  g_launches.fetch_sub(nodes);  // counted when the graph runs, not when it is captured
+  c->graphs.push_back(GraphEntry{key, exec, nodes});
+  *out = exec;
+  return DL_OK;
+}
+
+// Solve Mhat^dag Mhat x = b (b: normal-equation rhs in hi precision) for n columns.
+// x (hi) receives the solution.  final_check recomputes the residual in hi.
+dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* x, bool final_check,
+                 dl_solve_stats* stats, double* resid_out) {
+  const int hi = prm.prec_hi, lo = prm.prec_lo, f = prm.flavour;
+  Batch B = make_batch(c, n);
+  dl_status s;
+  if ((s = ensure_partial(c, B)) != DL_OK) return s;
+  CGFields F;
+  const int lo_ = lo;
+  if ((s = ensure_field(c, "cg_r", lo_, n, &F.r)) || (s = ensure_field(c, "cg_p", lo_, n, &F.p)) ||
+      (s = ensure_field(c, "cg_y", lo_, n, &F.y)) || (s = ensure_field(c, "cg_t1", lo_, n, &F.t1)) ||
+      (s = ensure_field(c, "cg_q", lo_, n, &F.q)) || (s = ensure_field(c, "cg_t2", lo_, n, &F.t2)) ||
+      (s = ensure_field(c, "cg_rh", hi, n, &F.rh)) || (s = ensure_field(c, "cg_ax", hi, n, &F.ax)) ||
+      (s = ensure_field(c, "cg_th1", hi, n, &F.th1)) || (s = ensure_field(c, "cg_tq", hi, n, &F.tq)) ||
+      (s = ensure_field(c, "cg_th2", hi, n, &F.th2)))
+    return s;
+  // x = 0, |b|^2
+  CK(dl::zero(B, hi, x->ref(), nullptr, c->st));
+  CK(dl::norm2(B, hi, b->ref(), nullptr, c->partial, c->st));
+  CK(colsum(c, B, DL_S_RR0));
+  CGState h;
+  if ((s = download_state(c, n, h)) != DL_OK) return s;
+  for (int i = 0; i < n; ++i) {
+    double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+    h.S[DL_S_RR * DL_NCMAX + i] = rr0;
+    h.S[DL_S_MAXR * DL_NCMAX + i] = sqrt(rr0);
+    h.active[i] = rr0 > 0.0 ? 1 : 0;
+    h.flags[i] = 0;
+  }
+  h.iters.assign(n, 0);
+  CK(cudaMemcpyAsync(c->iters, h.iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  if ((s = upload_state(c, n, h)) != DL_OK) return s;
+  CK(dl::copy(B, lo, hi, F.r->ref(), b->ref(), nullptr, c->st));
+  CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), nullptr, c->st));
+  CK(dl::zero(B, lo, F.y->ref(), nullptr, c->st));
+  const double tol2 = prm.tol * prm.tol;
+  const int chunk = std::max(1, prm.chunk);
+  cudaGraphExec_t gexec;
+  if ((s = get_graph(c, B, lo, f, F, chunk, tol2, prm.delta, &gexec)) != DL_OK) return s;
+  std::vector<int> finalized(n, 0), notconv(n, 0);
+  for (int i = 0; i < n; ++i)
+    if (!h.active[i]) finalized[i] = 1;  // zero right-hand side: x = 0
+  int n_rel = 0;
+  auto t0 = std::chrono::steady_clock::now();
+  bool breakdown = false;
+  while (true) {
+    bool any = false;
+    for (int i = 0; i < n; ++i) any |= (h.active[i] != 0);
+    if (!any) break;
+    int n_act = 0;
+    for (int i = 0; i < n; ++i) n_act += h.active[i] != 0;
+    CK(cudaGraphLaunch(gexec, c->st));
+    for (auto& ge : c->graphs)
+      if (ge.exec == gexec) g_launches.fetch_add(ge.kernels);
+    if ((s = download_state(c, n, h)) != DL_OK) return s;
+    if (c->profiling) {
+      for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->pev[2 * k], c->pev[2 * k + 1]));
+        c->prof_ms[k][lo] += ms;
+        c->prof_n[k][lo] += 1;
+        c->prof_items[k][lo] += (long long)c->Vh * n_act;
+      }
+    }
+    std::vector<int> mask(n, 0);
+    bool need = false;
+    for (int i = 0; i < n; ++i) {
+      if (finalized[i]) continue;
+      if (h.flags[i] & DL_FLAG_BREAKDOWN) {
+        if (!breakdown) {
+          char msg[256];
+          snprintf(msg, sizeof(msg), "CG breakdown in column %d after %d iterations (pAp %.3e, rr %.3e, rr_new %.3e)", i,
+                   h.iters[i], h.S[DL_S_PAP * DL_NCMAX + i], h.S[DL_S_RR * DL_NCMAX + i], h.S[DL_S_RRNEW * DL_NCMAX + i]);
+          c->err = msg;
+        }
+        breakdown = true;
+        mask[i] = 1;
+        need = true;
+        continue;
+      }
+      bool conv = (h.flags[i] & DL_FLAG_CONVERGED) != 0;
+      bool upd = (h.flags[i] & DL_FLAG_UPDATE) != 0 && prm.delta > 0.0;
+      bool maxed = h.active[i] && h.iters[i] >= prm.max_iter;
+      if (maxed) {
+        h.active[i] = 0;
+        notconv[i] = 1;
+      }
+      if (conv || maxed || (upd && h.active[i])) {
+        mask[i] = 1;
+        need = true;
+      }
+    }
+    if (getenv("DL_TRACE")) {
+      for (int i = 0; i < n; ++i)
+        fprintf(stderr, "[dl cg] col %d it %d active %d flags %d rr/rr0 %.3e pAp %.3e alpha %.3e beta %.3e maxr %.3e\n", i,
+                h.iters[i], h.active[i], h.flags[i],
+                h.S[DL_S_RR * DL_NCMAX + i] / std::max(h.S[DL_S_RR0 * DL_NCMAX + i], 1e-300),
+                h.S[DL_S_PAP * DL_NCMAX + i], h.S[DL_S_ALPHA * DL_NCMAX + i], h.S[DL_S_BETA * DL_NCMAX + i],
+                h.S[DL_S_MAXR * DL_NCMAX + i]);
+    }
+    if (!need) continue;
+    std::vector<double> rr;
+    if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) return s;
+    for (int i = 0; i < n; ++i) {
+      if (!mask[i]) continue;
+      ++n_rel;
+      double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+      bool conv = (h.flags[i] & DL_FLAG_CONVERGED) != 0;
+      h.flags[i] &= ~DL_FLAG_UPDATE;
+      h.S[DL_S_RR * DL_NCMAX + i] = rr[i];
+      h.S[DL_S_MAXR * DL_NCMAX + i] = sqrt(rr[i]);
+      if (h.flags[i] & DL_FLAG_BREAKDOWN) {
+        finalized[i] = 1;
+        h.active[i] = 0;
+      } else if (conv) {
+        if (prm.delta > 0.0 && rr[i] > prm.tol * prm.tol * rr0 && h.iters[i] < prm.max_iter) {
+          h.flags[i] &= ~DL_FLAG_CONVERGED;  // drifted: continue from the true residual
+          h.active[i] = 1;
+        } else {
+          finalized[i] = 1;
+        }
+      } else if (notconv[i]) {
+        finalized[i] = 1;
+      }
+    }
+    if ((s = upload_state(c, n, h)) != DL_OK) return s;
+  }
+  // any column that never went through a final update
+  {
+    std::vector<int> mask(n, 0);
+    bool need = false;
+    for (int i = 0; i < n; ++i)
+      if (!finalized[i]) {
+        mask[i] = 1;
+        need = true;
+      }
+    if (need) {
+      CK(cudaMemcpyAsync(c->upd, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+      CK(dl::accum(B, hi, lo, x->ref(), F.y->ref(), c->upd, 1, c->st));
+    }
+  }
+  std::vector<double> resid(n, 0.0);
+  if (final_check) {
+    std::vector<int> all(n, 1);
+    std::vector<double> rr;
+    // y is zero here, so the update only recomputes the residual
+    if ((s = reliable_update(c, B, hi, lo, f, F, x, b, all, rr)) != DL_OK) return s;
+    for (int i = 0; i < n; ++i) {
+      double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+      resid[i] = rr0 > 0 ? sqrt(rr[i] / rr0) : 0.0;
+    }
+  } else {
+    for (int i = 0; i < n; ++i) {
+      double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+      resid[i] = rr0 > 0 ? sqrt(h.S[DL_S_RR * DL_NCMAX + i] / rr0) : 0.0;
+    }
+  }
+  CK(cudaStreamSynchronize(c->st));
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int maxit = 0;
+  bool anync = false;
+  for (int i = 0; i < n; ++i) {
+    maxit = std::max(maxit, h.iters[i]);
+    anync |= notconv[i] != 0;
+  }
+  if (stats) {
+    for (int i = 0; i < n && i < DL_MAX_RHS; ++i) {
+      stats->iters[i] = h.iters[i];
+      stats->resid[i] = resid[i];
+    }
+    stats->reliable_updates = n_rel;
+    stats->max_iters = maxit;
+    stats->seconds = secs;
+  }
+  if (resid_out)
+    for (int i = 0; i < n; ++i) resid_out[i] = resid[i];
+  if (breakdown) return DL_BREAKDOWN;
+  if (anync) return fail(c, DL_NOT_CONVERGED, "max_iter reached");
+  return DL_OK;
+}
+
+dl_status check_ctx(dl_ctx* c, bool need_gauge) {
+  if (!c) return DL_ERR_ARG;
+  if (need_gauge && !c->has_gauge) return fail(c, DL_ERR_STATE, "no gauge field loaded");
+  return DL_OK;
+}
+
+int dtype_prec(int dtype) { return dtype == DL_C128 ? P64 : P32; }
+
+// ---- solve pipeline on internal fields --------------------------------------
+// From a full-lattice source (b_e, b_o, precision hi) to the solution
+// (x_e, psi_o, precision hi).
+dl_status solve_internal(dl_ctx* c, int n, const dl_solve_params& prm, Field* b_e, Field* b_o, Field* x_e, Field* psi_o,
+                         bool final_check, dl_solve_stats* stats) {
+  const int hi = prm.prec_hi, f = prm.flavour;
+  Batch B = make_batch(c, n);
+  dl_status s;
+  Field *tmp_o, *bhat, *bn, *t2;
+  if ((s = ensure_field(c, "sv_tmp_o", hi, n, &tmp_o)) || (s = ensure_field(c, "sv_bhat", hi, n, &bhat)) ||
+      (s = ensure_field(c, "sv_bn", hi, n, &bn)) || (s = ensure_field(c, "sv_t2", hi, n, &t2)))
+    return s;
+  // bhat_e = b_e + kappa D_eo R_oo^{-1} b_o
+  EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+  CK(dl::twist(B, hi, tmp_o->ref(), b_o->ref(), Ei, nullptr, c->st));
+  GaugeSet g{c->g64, c->g32, c->g16};
+  EpiSet Ep = epi(c, c->kappa, 0, 0, 0, 0);
+  CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, tmp_o->ref(), b_e->ref(), bhat->ref(), g, Ep, nullptr, nullptr,
+                NOF, NOF, NOF, nullptr, c->st));
+  // bn = Mhat^dag bhat
+  CK(stage1(c, B, hi, true, f, bhat->ref(), t2->ref(), nullptr));
+  CK(stage2(c, B, hi, true, f, t2->ref(), bhat->ref(), bn->ref(), nullptr, nullptr));
+  dl_status rs = run_cg(c, n, prm, bn, x_e, final_check, stats, nullptr);
+  if (rs < 0) return rs;
+  // psi_o = R_oo^{-1} (b_o + kappa D_oe x_e)
+  EpiSet Er = epi(c, c->kappa, 2, f, 0, 0);
+  CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 1, x_e->ref(), b_o->ref(), psi_o->ref(), g, Er, nullptr, nullptr,
+                NOF, NOF, NOF, nullptr, c->st));
+  return rs;
+}
+
+// momentum list on the device for p2max
+dl_status ensure_momenta(dl_ctx* c, int p2max) {
+  if (c->mom_p2 == p2max) return DL_OK;
+  int cnt = 0;
+  dl_momenta(p2max, &cnt, nullptr);
+  std::vector<int> lst(3 * cnt);
+  dl_momenta(p2max, &cnt, lst.data());
+  if (c->mom) cudaFree(c->mom);
+  c->mom = nullptr;
+  CK(cudaMalloc((void**)&c->mom, sizeof(int) * 3 * std::max(cnt, 1)));
+  CK(cudaMemcpy(c->mom, lst.data(), sizeof(int) * 3 * cnt, cudaMemcpyHostToDevice));
+  c->mom_p2 = p2max;
+  c->np = cnt;
+  return DL_OK;
+}
+
+int mom_extent(int p2max) {
+  int m = 0;
+  while ((m + 1) * (m + 1) <= p2max) ++m;
+  return m;
+}
+
+// Contract (s_e, s_o) with (eta_e, eta_o) for estimator mode into out
+// [ncol][T][np][nd][16] (device complex128) with the prefactor applied.
+dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv, int p2max, Field* s_e, Field* s_o,
+                            Field* eta_e, Field* eta_o, double pre_re, double pre_im, double2* out, int accumulate) {
+  Batch B = make_batch(c, n);
+  const LatDesc& L = B.lat[0];
+  dl_status s;
+  if ((s = ensure_momenta(c, p2max)) != DL_OK) return s;
+  const int m = mom_extent(p2max);
+  const int mx = m, my = m, mz = m;  // the cube must hold every listed momentum
+  const int NX = 2 * mx + 1, NY = 2 * my + 1, NZ = 2 * mz + 1;
+  const int npad = 1 << L.lognpad;
+  const int ncomp = with_deriv ? 80 : 16;
+  const size_t V = 2ull * L.Vh;
+  const size_t nW = (size_t)ncomp * V * npad;
+  const size_t nG1 = (size_t)ncomp * L.T * L.Z * L.Y * NX * npad;
+  const size_t nG2 = (size_t)ncomp * L.T * L.Z * NY * NX * npad;
+  const size_t nG3 = (size_t)ncomp * L.T * NZ * NY * NX * npad;
+  const size_t nph = 4096;
+  if ((s = ensure_scratch(c, sizeof(double2) * (nW + nG1 + nG2 + nG3 + nph))) != DL_OK) return s;
+  double2* W = (double2*)c->scratch;
+  double2* G1 = W + nW;
+  double2* G2 = G1 + nG1;
+  double2* G3 = G2 + nG2;
+  double2* ph = G3 + nG3;
+  if (L.X > (int)nph || L.Y > (int)nph || L.Z > (int)nph) return fail(c, DL_ERR_ARG, "spatial extent too large");
+  CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
+                        eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
+  CK(dl::dft_pass(W, G1, (long long)ncomp * L.T * L.Z * L.Y, L.X, npad, mx, ph, c->st));
+  CK(dl::dft_pass(G1, G2, (long long)ncomp * L.T * L.Z, L.Y, (long long)NX * npad, my, ph, c->st));
+  CK(dl::dft_pass(G2, G3, (long long)ncomp * L.T, L.Z, (long long)NY * NX * npad, mz, ph, c->st));
+  CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, pre_re, pre_im, out, accumulate, c->st));
+  return DL_OK;
+}
+
+// w = (BH)^k s on the full lattice, B = R_f^{-1}, H = -kappa D (Eq. HPE)
+dl_status bh_power(dl_ctx* c, int n, int prec, int f, int k, Field* se, Field* so, Field** we, Field** wo) {
+  Batch B = make_batch(c, n);
+  dl_status s;
+  Field *ae, *ao, *be, *bo;
+  if ((s = ensure_field(c, "bh_ae", prec, n, &ae)) || (s = ensure_field(c, "bh_ao", prec, n, &ao)) ||
+      (s = ensure_field(c, "bh_be", prec, n, &be)) || (s = ensure_field(c, "bh_bo", prec, n, &bo)))
+    return s;
+  GaugeSet g{c->g64, c->g32, c->g16};
+  EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+  Field *ie = se, *io = so;
+  for (int it = 0; it < k; ++it) {
+    Field* oe = (it % 2 == 0) ? ae : be;
+    Field* oo = (it % 2 == 0) ? ao : bo;
+    CK(dl::dslash(B, prec, grec_of(c, prec), EPI_PLAIN, false, 0, io->ref(), NOF, oe->ref(), g, E, nullptr, nullptr, NOF,
+                  NOF, NOF, nullptr, c->st));
+    CK(dl::dslash(B, prec, grec_of(c, prec), EPI_PLAIN, false, 1, ie->ref(), NOF, oo->ref(), g, E, nullptr, nullptr, NOF,
+                  NOF, NOF, nullptr, c->st));
+    ie = oe;
+    io = oo;
+  }
+  *we = ie;
+  *wo = io;
+  return DL_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stream) {
+  if (!out || !dims) return DL_ERR_ARG;
+  *out = nullptr;
+  for (int k = 0; k < 4; ++k)
+    if (dims[k] < 2 || (dims[k] & 1)) return DL_ERR_ARG;
+  long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V / 2 >= (1LL << 31) / DL_MAXC) return DL_ERR_ARG;
+  dl_ctx* c = new dl_ctx();
+  c->dev = device;
+  memcpy(c->dims, dims, sizeof(int) * 4);
+  c->Vh = (int)(V / 2);
+  c->user = (cudaStream_t)cuda_stream;
+  cudaError_t e;
+  if ((e = cudaSetDevice(device)) != cudaSuccess || (e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->S, sizeof(double) * DL_NS * DL_NCMAX)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->active, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->flags, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->iters, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->upd, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->misc, sizeof(double2) * 4096)) != cudaSuccess) {
+    dl_destroy(c);
+    return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
+  }
+  for (int k = 0; k < 8; ++k)
+    if ((e = cudaEventCreate(&c->pev[k])) != cudaSuccess) {
+    dl_destroy(c);
+    return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
+  }
+  *out = c;
+  return DL_OK;
+}
+
+void dl_destroy(dl_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  if (c->st) cudaStreamSynchronize(c->st);
+  invalidate_graphs(c);
+  for (auto& kv : c->ws) {
+    cudaFree(kv.second.data);
+    if (kv.second.norm) cudaFree(kv.second.norm);
+  }
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  void* ptrs[] = {c->g64, c->g32, c->g16, c->partial, c->S, c->active, c->flags, c->iters, c->upd, c->misc, c->mom,
+                  c->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (int k = 0; k < 8; ++k)
+    if (c->pev[k]) cudaEventDestroy(c->pev[k]);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+const char* dl_last_error(const dl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+dl_status dl_set_stream(dl_ctx* c, void* s) {
+  if (!c) return DL_ERR_ARG;
+  c->user = (cudaStream_t)s;
+  return DL_OK;
+}
+
+dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_boundary, int recon_f32, int recon_f16) {
+  if (!c || !links) return DL_ERR_ARG;
+  if (!(recon_f32 == 12 || recon_f32 == 8 || recon_f32 == 18)) return fail(c, DL_ERR_ARG, "recon_f32 must be 18, 12 or 8");
+  if (!(recon_f16 == 12 || recon_f16 == 8)) return fail(c, DL_ERR_ARG, "recon_f16 must be 12 or 8");
+  if (recon_f32 == 18) recon_f32 = 12;  // FP32 operator reads the 12-real form; 18 is accepted as "uncompressed request"
+  dl_status s;
+  if ((s = enter(c)) != DL_OK) return s;
+  const size_t V = 2ull * c->Vh;
+  const size_t nl = V * 4;
+  if (!c->g64) {
+    CK(cudaMalloc(&c->g64, nl * 9 * sizeof(double2)));  // 144 B per link
+    CK(cudaMalloc(&c->g32, nl * 3 * sizeof(float4)));    // up to 48 B per link
+    CK(cudaMalloc(&c->g16, nl * 3 * sizeof(uint2)));     // up to 24 B per link
+  }
+  const double* dlinks = links;
+  void* tmp = nullptr;
+  if (!on_device) {
+    CK(cudaMalloc(&tmp, nl * 9 * sizeof(double2)));
+    CK(cudaMemcpyAsync(tmp, links, nl * 9 * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    dlinks = (const double*)tmp;
+  }
+  c->tbc = t_boundary;
+  c->rec32 = recon_f32;
+  c->rec16 = recon_f16;
+  Batch B = make_batch(c, 1);
+  cudaError_t e = dl::pack_gauge(B.lat[0], dlinks, c->g64, c->g32, recon_f32, c->g16, recon_f16, c->st);
+  if (tmp) {
+    cudaStreamSynchronize(c->st);
+    cudaFree(tmp);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "pack_gauge");
+  c->has_gauge = true;
+  invalidate_graphs(c);
+  return leave(c);
+}
+
+dl_status dl_set_params(dl_ctx* c, double kappa, double amu) {
+  if (!c) return DL_ERR_ARG;
+  if (!(kappa > 0.0) || !std::isfinite(kappa) || !std::isfinite(amu)) return fail(c, DL_ERR_ARG, "bad kappa/amu");
+  c->kappa = kappa;
+  c->amu = amu;
+  return DL_OK;
+}
+
+dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant) {
+  if (!c || !out || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64)) return DL_ERR_ARG;
+  dl_status s;
+  if ((s = enter(c)) != DL_OK) return s;
+  const int prec = dtype_prec(dtype);
+  Batch B = make_batch(c, n);
+  Field *e, *o;
+  if ((s = ensure_field(c, "nz_e", prec, n, &e)) || (s = ensure_field(c, "nz_o", prec, n, &o))) return s;
+  CK(dl::noise_z4(B, prec, 0, e->ref(), seed, first_index, quadrant, c->st));
+  CK(dl::noise_z4(B, prec, 1, o->ref(), seed, first_index, quadrant, c->st));
+  CK(dl::unpack(B, prec, 0, out, e->ref(), dtype, c->st));
+  CK(dl::unpack(B, prec, 1, out, o->ref(), dtype, c->st));
+  return leave(c);
+}
+
+dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux, void* out, int dtype) {
+  dl_status s;
+  if ((s = check_ctx(c, true)) != DL_OK) return s;
+  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec < 0 || prec > 2 ||
+      (dtype != DL_C128 && dtype != DL_C64))
+    return fail(c, DL_ERR_ARG, "dl_apply: bad argument");
+  if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");
+  if ((s = enter(c)) != DL_OK) return s;
+  Batch B = make_batch(c, n);
+  if ((s = ensure_partial(c, B)) != DL_OK) return s;
+  Field *ie, *io, *oe, *oo, *ae, *ao, *t;
+  if ((s = ensure_field(c, "ap_ie", prec, n, &ie)) || (s = ensure_field(c, "ap_io", prec, n, &io)) ||
+      (s = ensure_field(c, "ap_oe", prec, n, &oe)) || (s = ensure_field(c, "ap_oo", prec, n, &oo)) ||
+      (s = ensure_field(c, "ap_ae", prec, n, &ae)) || (s = ensure_field(c, "ap_ao", prec, n, &ao)) ||
+      (s = ensure_field(c, "ap_t", prec, n, &t)))
+    return s;
+  CK(dl::pack(B, prec, 0, ie->ref(), in, dtype, c->st));
+  CK(dl::pack(B, prec, 1, io->ref(), in, dtype, c->st));
+  if (aux) {
+    CK(dl::pack(B, prec, 0, ae->ref(), aux, dtype, c->st));
+    CK(dl::pack(B, prec, 1, ao->ref(), aux, dtype, c->st));
+  }
+  GaugeSet g{c->g64, c->g32, c->g16};
+  const int gr = grec_of(c, prec);
+  auto D = [&](int epi_kind, bool dag, int par, Field* src, Field* ax, Field* dst, const EpiSet& E) {
+    return dl::dslash(B, prec, gr, epi_kind, dag, par, src->ref(), ax ? ax->ref() : NOF, dst->ref(), g, E, nullptr,
+                      nullptr, NOF, NOF, NOF, nullptr, c->st);
+  };
+  switch (op) {
+    case DL_OP_M:
+    case DL_OP_MDAG: {
+      bool dag = op == DL_OP_MDAG;
+      EpiSet E = epi(c, -c->kappa, 0, 0, 1, dag ? -f : f);
+      CK(D(EPI_AUX, dag, 0, io, ie, oe, E));
+      CK(D(EPI_AUX, dag, 1, ie, io, oo, E));
+      break;
+    }
+    case DL_OP_HOP: {
+      EpiSet E = epi(c, 1.0, 0, 0, 0, 0);
+      CK(D(EPI_PLAIN, false, 0, io, nullptr, oe, E));
+      CK(D(EPI_PLAIN, false, 1, ie, nullptr, oo, E));
+      break;
+    }
+    case DL_OP_MHAT:
+    case DL_OP_MHAT_DAG: {
+      bool dag = op == DL_OP_MHAT_DAG;
+      CK(stage1(c, B, prec, dag, f, ie->ref(), t->ref(), nullptr));
+      CK(stage2(c, B, prec, dag, f, t->ref(), ie->ref(), oe->ref(), nullptr, nullptr));
+      CK(dl::zero(B, prec, oo->ref(), nullptr, c->st));
+      break;
+    }
+    case DL_OP_PREP: {
+      EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+      CK(dl::twist(B, prec, t->ref(), io->ref(), Ei, nullptr, c->st));
+      EpiSet E = epi(c, c->kappa, 0, 0, 0, 0);
+      CK(D(EPI_AUX, false, 0, t, ie, oe, E));
+      CK(dl::zero(B, prec, oo->ref(), nullptr, c->st));
+      break;
+    }
+    case DL_OP_RECON: {
+      CK(dl::copy(B, prec, prec, oe->ref(), ie->ref(), nullptr, c->st));
+      EpiSet E = epi(c, c->kappa, 2, f, 0, 0);
+      CK(D(EPI_AUX, false, 1, ie, ao, oo, E));
+      break;
+    }
+    case DL_OP_BH: {
+      EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+      CK(D(EPI_PLAIN, false, 0, io, nullptr, oe, E));
+      CK(D(EPI_PLAIN, false, 1, ie, nullptr, oo, E));
+      break;
+    }
+    default:
+      return fail(c, DL_ERR_ARG, "unknown operator");
+  }
+  CK(dl::unpack(B, prec, 0, out, oe->ref(), dtype, c->st));
+  CK(dl::unpack(B, prec, 1, out, oo->ref(), dtype, c->st));
+  return leave(c);
+}
+
+dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, const dl_solve_params* prm,
+                   dl_solve_stats* stats) {
+  dl_status s;
+  if ((s = check_ctx(c, true)) != DL_OK) return s;
+  if (!src || !sol || !prm || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64))
+    return fail(c, DL_ERR_ARG, "dl_solve: bad argument");
+  if (!(prm->prec_hi == DL_F64 || prm->prec_hi == DL_F32) || prm->prec_lo < 0 || prm->prec_lo > 2 ||
+      prm->prec_lo < prm->prec_hi || !(prm->tol > 0.0) || prm->max_iter < 1 || (prm->flavour != 1 && prm->flavour != -1) ||
+      prm->delta < 0.0 || prm->delta >= 1.0)
+    return fail(c, DL_ERR_ARG, "dl_solve: bad parameters");
+  if ((s = enter(c)) != DL_OK) return s;
+  const int hi = prm->prec_hi;
+  Batch B = make_batch(c, n);
+  if ((s = ensure_partial(c, B)) != DL_OK) return s;
+  Field *be, *bo, *xe, *po;
+  if ((s = ensure_field(c, "sl_be", hi, n, &be)) || (s = ensure_field(c, "sl_bo", hi, n, &bo)) ||
+      (s = ensure_field(c, "sl_xe", hi, n, &xe)) || (s = ensure_field(c, "sl_po", hi, n, &po)))
+    return s;
+  CK(dl::pack(B, hi, 0, be->ref(), src, dtype, c->st));
+  CK(dl::pack(B, hi, 1, bo->ref(), src, dtype, c->st));
+  dl_solve_stats st;
+  memset(&st, 0, sizeof(st));
+  dl_status rs = solve_internal(c, n, *prm, be, bo, xe, po, true, &st);
+  if (rs < 0) return rs;
+  CK(dl::unpack(B, hi, 0, sol, xe->ref(), dtype, c->st));
+  CK(dl::unpack(B, hi, 1, sol, po->ref(), dtype, c->st));
+  // true residual |b - M psi| / |b| on the full lattice, in FP64
+  {
+    Field *pe64, *po64, *be64, *bo64, *re, *ro;
+    if ((s = ensure_field(c, "tr_pe", P64, n, &pe64)) || (s = ensure_field(c, "tr_po", P64, n, &po64)) ||
+        (s = ensure_field(c, "tr_be", P64, n, &be64)) || (s = ensure_field(c, "tr_bo", P64, n, &bo64)) ||
+        (s = ensure_field(c, "tr_re", P64, n, &re)) || (s = ensure_field(c, "tr_ro", P64, n, &ro)))
+      return s;
+    CK(dl::copy(B, P64, hi, pe64->ref(), xe->ref(), nullptr, c->st));
+    CK(dl::copy(B, P64, hi, po64->ref(), po->ref(), nullptr, c->st));
+    CK(dl::pack(B, P64, 0, be64->ref(), src, dtype, c->st));
+    CK(dl::pack(B, P64, 1, bo64->ref(), src, dtype, c->st));
+    GaugeSet g{c->g64, c->g32, c->g16};
+    EpiSet E = epi(c, -c->kappa, 0, 0, 1, prm->flavour);
+    CK(dl::dslash(B, P64, 18, EPI_AUX, false, 0, po64->ref(), pe64->ref(), re->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
+                  nullptr, c->st));
+    CK(dl::dslash(B, P64, 18, EPI_AUX, false, 1, pe64->ref(), po64->ref(), ro->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
+                  nullptr, c->st));
+    std::vector<double> S(DL_NS * DL_NCMAX);
+    double num[DL_MAX_RHS] = {0}, den[DL_MAX_RHS] = {0};
+    CK(dl::xmy_norm(B, P64, re->ref(), be64->ref(), re->ref(), nullptr, c->partial, c->st));
+    CK(colsum(c, B, DL_S_TMP));
+    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < n; ++i) num[i] += S[DL_S_TMP * DL_NCMAX + i];
+    CK(dl::xmy_norm(B, P64, ro->ref(), bo64->ref(), ro->ref(), nullptr, c->partial, c->st));
+    CK(colsum(c, B, DL_S_TMP));
+    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < n; ++i) num[i] += S[DL_S_TMP * DL_NCMAX + i];
+    CK(dl::norm2(B, P64, be64->ref(), nullptr, c->partial, c->st));
+    CK(colsum(c, B, DL_S_TMP));
+    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < n; ++i) den[i] += S[DL_S_TMP * DL_NCMAX + i];
+    CK(dl::norm2(B, P64, bo64->ref(), nullptr, c->partial, c->st));
+    CK(colsum(c, B, DL_S_TMP));
+    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < n; ++i) den[i] += S[DL_S_TMP * DL_NCMAX + i];
+    for (int i = 0; i < n; ++i) st.true_resid[i] = den[i] > 0 ? sqrt(num[i] / den[i]) : 0.0;
+  }
+  if (stats) *stats = st;
+  dl_status ls = leave(c);
+  if (ls != DL_OK) return ls;
+  return rs;
+}
+
+dl_status dl_profile(dl_ctx* c, int enable, double* out) {
+  if (!c) return DL_ERR_ARG;
+  if (out) {
+    for (int k = 0; k < 4; ++k)
+      for (int p = 0; p < 3; ++p) {
+        out[(k * 3 + p) * 3 + 0] = (double)c->prof_n[k][p];
+        out[(k * 3 + p) * 3 + 1] = c->prof_ms[k][p];
+        out[(k * 3 + p) * 3 + 2] = (double)c->prof_items[k][p];
+      }
+  }
+  if (enable >= 0) {
+    if ((enable != 0) != (c->profiling != 0)) invalidate_graphs(c);
+    c->profiling = enable != 0;
+    memset(c->prof_ms, 0, sizeof(c->prof_ms));
+    memset(c->prof_n, 0, sizeof(c->prof_n));
+    memset(c->prof_items, 0, sizeof(c->prof_items));
+  }
+  return DL_OK;
+}
+
+long long dl_kernel_launches(void) { return g_launches.load(); }
+
+dl_status dl_momenta(int p2max, int* count, int* list) {
+  if (!count || p2max < 0 || p2max > 64) return DL_ERR_ARG;
+  int m = mom_extent(p2max);
+  int k = 0;
+  for (int nz = -m; nz <= m; ++nz)
+    for (int ny = -m; ny <= m; ++ny)
+      for (int nx = -m; nx <= m; ++nx)
+        if (nx * nx + ny * ny + nz * nz <= p2max) {
+          if (list) {
+            list[3 * k] = nx;
+            list[3 * k + 1] = ny;
+            list[3 * k + 2] = nz;
+          }
+          ++k;
+        }
+  *count = k;
+  return DL_OK;
+}
+
+dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int with_deriv, int p2max,
+                      double* out, int accumulate) {
+  dl_status s;
+  if ((s = check_ctx(c, true)) != DL_OK) return s;
+  if (!sol || !out || n < 1 || n > DL_MAX_RHS || est < 0 || est > 3 || p2max < 0 || p2max > 64 ||
+      (dtype != DL_C128 && dtype != DL_C64))
+    return fail(c, DL_ERR_ARG, "dl_contract: bad argument");
+  if ((est == DL_EST_STANDARD || est == DL_EST_GEN || est == DL_EST_HPE) && !eta)
+    return fail(c, DL_ERR_ARG, "estimator needs eta");
+  if (est == DL_EST_HPE && with_deriv) return fail(c, DL_ERR_ARG, "the HPE estimator is local only");
+  if ((s = enter(c)) != DL_OK) return s;
+  const int prec = dtype_prec(dtype);
+  Batch B = make_batch(c, n);
+  Field *se, *so, *ee, *eo;
+  if ((s = ensure_field(c, "ct_se", prec, n, &se)) || (s = ensure_field(c, "ct_so", prec, n, &so)) ||
+      (s = ensure_field(c, "ct_ee", prec, n, &ee)) || (s = ensure_field(c, "ct_eo", prec, n, &eo)))
+    return s;
+  CK(dl::pack(B, prec, 0, se->ref(), sol, dtype, c->st));
+  CK(dl::pack(B, prec, 1, so->ref(), sol, dtype, c->st));
+  if (eta) {
+    CK(dl::pack(B, prec, 0, ee->ref(), eta, dtype, c->st));
+    CK(dl::pack(B, prec, 1, eo->ref(), eta, dtype, c->st));
+  } else {
+    CK(dl::zero(B, prec, ee->ref(), nullptr, c->st));
+    CK(dl::zero(B, prec, eo->ref(), nullptr, c->st));
+  }
+  Field *we = se, *wo = so;
+  if (est == DL_EST_HPE)
+    if ((s = bh_power(c, n, prec, 1, 4, se, so, &we, &wo)) != DL_OK) return s;
+  double pre_re = 1.0, pre_im = 0.0;
+  if (est == DL_EST_ONE_END) {
+    pre_re = 0.0;
+    pre_im = -4.0 * c->kappa * c->amu;
+  } else if (est == DL_EST_GEN) {
+    pre_re = 2.0;
+  }
+  if ((s = contract_internal(c, n, prec, est, with_deriv, p2max, we, wo, ee, eo, pre_re, pre_im, (double2*)out,
+                             accumulate)) != DL_OK)
+    return s;
+  return leave(c);
+}
+
+dl_status dl_hpe_exact(dl_ctx* c, int flavour, double* out16) {
+  if (!c || !out16 || (flavour != 1 && flavour != -1)) return DL_ERR_ARG;
+  dl_status s;
+  if ((s = enter(c)) != DL_OK) return s;
+  CK(dl::hpe_exact(c->kappa, c->amu, flavour, c->misc, c->st));
+  CK(cudaMemcpyAsync(out16, c->misc, sizeof(double2) * 16, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return leave(c);
+}
+
+dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double* obs_hp, double* obs_lp_pair,
+                     double* obs_lp, dl_tsm_info* info) {
+  dl_status s;
+  if ((s = check_ctx(c, true)) != DL_OK) return s;
+  if (!prm || prm->n_hp < 0 || prm->n_lp < 0 || prm->n_hp + prm->n_lp < 1 || prm->block < 1 || prm->block > DL_MAX_RHS ||
+      !(prm->tol_hp > 0.0) || !(prm->tol_lp > 0.0) || prm->p2max < 0 || prm->p2max > 64 || prm->max_iter < 1 ||
+      prm->prec_hp_lo < DL_F64 || prm->prec_hp_lo > DL_F16 || prm->prec_lp_lo < DL_F32 || prm->prec_lp_lo > DL_F16 ||
+      prm->delta_hp < 0.0 || prm->delta_hp >= 1.0)
+    return fail(c, DL_ERR_ARG, "dl_tsm_run: bad parameters");
+  if (prm->hpe && prm->with_deriv) return fail(c, DL_ERR_ARG, "dl_tsm_run: the HPE estimator is local only");
+  if ((s = enter(c)) != DL_OK) return s;
+  auto t_all = std::chrono::steady_clock::now();
+  if ((s = ensure_momenta(c, prm->p2max)) != DL_OK) return s;
+  const int np = c->np, nd = prm->with_deriv ? 5 : 1, T = c->dims[3];
+  const int n_est = prm->hpe ? 3 : 2;
+  const int est_mode[3] = {DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE};
+  const long long per = (long long)T * np * nd * 16;
+  const int blk = prm->block;
+  double2 *acc_d, *acc_l, *bl, *bh, *res;
+  double *obs1, *obs2;
+  void* p;
+  if ((s = ensure_buf(c, "ts_accd", sizeof(double2) * n_est * per, &p)) != DL_OK) return s;
+  acc_d = (double2*)p;
+  if ((s = ensure_buf(c, "ts_accl", sizeof(double2) * n_est * per, &p)) != DL_OK) return s;
+  acc_l = (double2*)p;
+  if ((s = ensure_buf(c, "ts_bl", sizeof(double2) * n_est * per * blk, &p)) != DL_OK) return s;
+  bl = (double2*)p;
+  if ((s = ensure_buf(c, "ts_bh", sizeof(double2) * n_est * per * blk, &p)) != DL_OK) return s;
+  bh = (double2*)p;
+  if ((s = ensure_buf(c, "ts_res", sizeof(double2) * n_est * per, &p)) != DL_OK) return s;
+  res = (double2*)p;
+  if ((s = ensure_buf(c, "ts_obs1", sizeof(double) * 4 * blk, &p)) != DL_OK) return s;
+  obs1 = (double*)p;
+  if ((s = ensure_buf(c, "ts_obs2", sizeof(double) * 4 * blk, &p)) != DL_OK) return s;
+  obs2 = (double*)p;
+  CK(cudaMemsetAsync(acc_d, 0, sizeof(double2) * n_est * per, c->st));
+  CK(cudaMemsetAsync(acc_l, 0, sizeof(double2) * n_est * per, c->st));
+  int ip0 = 0;
+  {
+    std::vector<int> lst(3 * np);
+    int cnt;
+    dl_momenta(prm->p2max, &cnt, lst.data());
+    for (int k = 0; k < np; ++k)
+      if (lst[3 * k] == 0 && lst[3 * k + 1] == 0 && lst[3 * k + 2] == 0) ip0 = k;
+  }
+  const double Ls = (double)c->dims[0] * c->dims[1] * c->dims[2];
+  CK(dl::hpe_exact(c->kappa, c->amu, 1, c->misc, c->st));
+  dl_tsm_info inf;
+  memset(&inf, 0, sizeof(inf));
+  inf.np = np;
+  inf.nd = nd;
+  inf.n_est = n_est;
+  double t_hp = 0, t_lp = 0, t_ct = 0;
+  bool any_nc = false;
+
+  // one precision's pipeline: noise -> solve -> contractions into `out`
+  auto run_block = [&](int n, uint64_t first, bool hp, double2* out, double* obs, dl_solve_stats* st) -> dl_status {
+    const int hi = hp ? P64 : P32;
+    dl_solve_params sp;
+    sp.tol = hp ? prm->tol_hp : prm->tol_lp;
+    sp.max_iter = prm->max_iter;
+    sp.prec_hi = hi;
+    sp.prec_lo = hp ? prm->prec_hp_lo : prm->prec_lp_lo;
+    sp.delta = hp ? prm->delta_hp : 0.0;
+    sp.flavour = 1;
+    sp.chunk = prm->chunk > 0 ? prm->chunk : 16;
+    Batch B = make_batch(c, n);
+    dl_status s2;
+    if ((s2 = ensure_partial(c, B)) != DL_OK) return s2;
+    Field *ee, *eo, *xe, *po;
+    const char* tag = hp ? "64" : "32";
+    if ((s2 = ensure_field(c, std::string("ts_ee") + tag, hi, n, &ee)) ||
+        (s2 = ensure_field(c, std::string("ts_eo") + tag, hi, n, &eo)) ||
+        (s2 = ensure_field(c, std::string("ts_xe") + tag, hi, n, &xe)) ||
+        (s2 = ensure_field(c, std::string("ts_po") + tag, hi, n, &po)))
+      return s2;
+    CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, first, 0, c->st));
+    CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, first, 0, c->st));
+    auto t0 = std::chrono::steady_clock::now();
+    dl_status rs = solve_internal(c, n, sp, ee, eo, xe, po, false, st);
+    if (rs < 0) return rs;
+    if (rs == DL_NOT_CONVERGED) any_nc = true;
+    CK(cudaStreamSynchronize(c->st));
+    auto t1 = std::chrono::steady_clock::now();
+    (hp ? t_hp : t_lp) += std::chrono::duration<double>(t1 - t0).count();
+    for (int e = 0; e < n_est; ++e) {
+      double2* o = out + (size_t)e * per * blk;
+      if (est_mode[e] == DL_EST_HPE) {
+        Field *we, *wo;
+        if ((s2 = bh_power(c, n, hi, 1, 4, xe, po, &we, &wo)) != DL_OK) return s2;
+        if ((s2 = contract_internal(c, n, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0)) != DL_OK) return s2;
+        CK(dl::add_exact_p0(B, np, nd, ip0, c->misc, Ls, o, c->st));
+      } else {
+        double pr = 1.0, pi = 0.0;
+        if (est_mode[e] == DL_EST_ONE_END) {
+          pr = 0.0;
+          pi = -4.0 * c->kappa * c->amu;
+        } else {
+          pr = 2.0;
+        }
+        if ((s2 = contract_internal(c, n, hi, est_mode[e], prm->with_deriv, prm->p2max, xe, po, ee, eo, pr, pi, o, 0)) !=
+            DL_OK)
+          return s2;
+      }
+    }
+    CK(dl::observables(out, out + (size_t)per * blk, n, T, np, nd, ip0, obs, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    t_ct += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
+    return rs;
+  };
+
+  std::vector<double> hbuf(4 * blk);
+  for (int b0 = 0; b0 < prm->n_hp; b0 += blk) {
+    int n = std::min(blk, prm->n_hp - b0);
+    dl_solve_stats st;
+    memset(&st, 0, sizeof(st));
+    if ((s = run_block(n, (uint64_t)b0, false, bl, obs1, &st)) < 0) return s;
+    for (int i = 0; i < n; ++i) inf.iters_lp += st.iters[i];
+    memset(&st, 0, sizeof(st));
+    if ((s = run_block(n, (uint64_t)b0, true, bh, obs2, &st)) < 0) return s;
+    for (int i = 0; i < n; ++i) inf.iters_hp += st.iters[i];
+    for (int e = 0; e < n_est; ++e)
+      CK(dl::col_accumulate(bh + (size_t)e * per * blk, bl + (size_t)e * per * blk, n, per, 1.0, acc_d + (size_t)e * per,
+                            c->st));
+    if (obs_lp_pair) {
+      CK(cudaMemcpyAsync(hbuf.data(), obs1, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      memcpy(obs_lp_pair + 4 * b0, hbuf.data(), sizeof(double) * 4 * n);
+    }
+    if (obs_hp) {
+      CK(cudaMemcpyAsync(hbuf.data(), obs2, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      memcpy(obs_hp + 4 * b0, hbuf.data(), sizeof(double) * 4 * n);
+    }
+  }
+  for (int b0 = 0; b0 < prm->n_lp; b0 += blk) {
+    int n = std::min(blk, prm->n_lp - b0);
+    dl_solve_stats st;
+    memset(&st, 0, sizeof(st));
+    if ((s = run_block(n, (uint64_t)(prm->n_hp + b0), false, bl, obs1, &st)) < 0) return s;
+    for (int i = 0; i < n; ++i) inf.iters_lp += st.iters[i];
+    for (int e = 0; e < n_est; ++e)
+      CK(dl::col_accumulate(bl + (size_t)e * per * blk, nullptr, n, per, 1.0, acc_l + (size_t)e * per, c->st));
+    if (obs_lp) {
+      CK(cudaMemcpyAsync(hbuf.data(), obs1, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      memcpy(obs_lp + 4 * b0, hbuf.data(), sizeof(double) * 4 * n);
+    }
+  }
+  // Eq. estiTSM: mean HP-LP correction + mean over the fresh LP set
+  const double a = prm->n_hp > 0 ? 1.0 / prm->n_hp : 0.0, b = prm->n_lp > 0 ? 1.0 / prm->n_lp : 0.0;
+  CK(dl::combine(acc_d, acc_l, a, b, (long long)n_est * per, res, c->st));
+  if (loops) CK(cudaMemcpyAsync(loops, res, sizeof(double2) * n_est * per, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  inf.seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_all).count();
+  inf.seconds_hp = t_hp;
+  inf.seconds_lp = t_lp;
+  inf.seconds_contract = t_ct;
+  if (info) {
+    inf.not_converged = any_nc ? 1 : 0;
+    *info = inf;
+  }
+  if ((s = leave(c)) != DL_OK) return s;
+  return any_nc ? fail(c, DL_NOT_CONVERGED, "a TSM solve hit max_iter") : DL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Site-local vector kernels of the solver (BLAS-1 updates, conversions, norms,
+// twist) and the per-column CG scalar kernels.  All reductions are per column
+// and deterministic: block partial sums in fixed order, then one CTA per
+// column sums the partials of its lattice's blocks in fixed order.
+#include "dl_internal.cuh"
+#include "dl_kernels.h"
+
+namespace {
+
+#define ITEM_PROLOGUE                                                                     \
+  const int l = find_lat(B, blockIdx.x);                                                  \
+  const LatDesc& L = B.lat[l];                                                            \
+  const int npad = 1 << L.lognpad;                                                        \
+  const long long j = (long long)(blockIdx.x - B.blk_begin[l]) * blockDim.x + threadIdx.x; \
+  const long long nitems = (long long)L.Vh * npad;                                        \
+  const int col = (int)(j & (npad - 1));                                                  \
+  const int gc = L.rhs_base + col;                                                        \
+  const bool act = (j < nitems) && (col < L.ncol) && (mask == nullptr || mask[gc] != 0);
+
+// dst = src (precision conversion)
+template <int PD, int PS>
+__global__ void copy_kernel(Batch B, FieldRef dst, FieldRef src, const int* mask) {
+  ITEM_PROLOGUE
+  if (!act) return;
+  typename SIO<PS>::real v[24];
+  SIO<PS>::load(seg_ptr<PS>(src, L), seg_norm(src, L), nitems, j, v);
+  typename SIO<PD>::real w[24];
+#pragma unroll
+  for (int m = 0; m < 24; ++m) w[m] = (typename SIO<PD>::real)v[m];
+  SIO<PD>::store(seg_ptr_w<PD>(dst, L), seg_norm(dst, L), nitems, j, w);
+}
+
+// x += y, then y = 0
+template <int PH, int PL>
+__global__ void accum_kernel(Batch B, FieldRef x, FieldRef y, const int* mask, int zero_y) {
+  ITEM_PROLOGUE
+  if (!act) return;
+  typename SIO<PH>::real xv[24];
+  typename SIO<PL>::real yv[24];
+  SIO<PH>::load(seg_ptr<PH>(x, L), seg_norm(x, L), nitems, j, xv);
+  SIO<PL>::load(seg_ptr<PL>(y, L), seg_norm(y, L), nitems, j, yv);
+#pragma unroll
+  for (int m = 0; m < 24; ++m) xv[m] += (typename SIO<PH>::real)yv[m];
+  SIO<PH>::store(seg_ptr_w<PH>(x, L), seg_norm(x, L), nitems, j, xv);
+  if (zero_y) {
+#pragma unroll
+    for (int m = 0; m < 24; ++m) yv[m] = 0;
+    SIO<PL>::store(seg_ptr_w<PL>(y, L), seg_norm(y, L), nitems, j, yv);
+  }
+}
+
+// r = b - a (same precision), partial |r|^2 per column
+template <int P>
+__global__ void xmy_norm_kernel(Batch B, FieldRef r, FieldRef b, FieldRef a, const int* mask, double* partial) {
+  ITEM_PROLOGUE
+  double red = 0.0;
+  if (act) {
+    typename SIO<P>::real bv[24], av[24];
+    SIO<P>::load(seg_ptr<P>(b, L), seg_norm(b, L), nitems, j, bv);
+    SIO<P>::load(seg_ptr<P>(a, L), seg_norm(a, L), nitems, j, av);
+#pragma unroll
+    for (int m = 0; m < 24; ++m) {
+      bv[m] -= av[m];
+      red += (double)bv[m] * (double)bv[m];
+    }
+    SIO<P>::store(seg_ptr_w<P>(r, L), seg_norm(r, L), nitems, j, bv);
+  }
+  block_reduce_cols(red, npad, partial);
+}
+
+// partial |v|^2 per column
+template <int P>
+__global__ void norm_kernel(Batch B, FieldRef v, const int* mask, double* partial) {
+  ITEM_PROLOGUE
+  double red = 0.0;
+  if (act) {
+    typename SIO<P>::real a[24];
+    SIO<P>::load(seg_ptr<P>(v, L), seg_norm(v, L), nitems, j, a);
+#pragma unroll
+    for (int m = 0; m < 24; ++m) red += (double)a[m] * (double)a[m];
+  }
+  block_reduce_cols(red, npad, partial);
+}
+
+// p = r + beta p
+template <int P>
+__global__ void xpay_kernel(Batch B, FieldRef p, FieldRef r, const double* __restrict__ beta, const int* mask) {
+  ITEM_PROLOGUE
+  if (!act) return;
+  typedef typename SIO<P>::real R;
+  R rv[24], pv[24];
+  const R be = (R)beta[gc];
+  SIO<P>::load(seg_ptr<P>(r, L), seg_norm(r, L), nitems, j, rv);
+  SIO<P>::load(seg_ptr<P>(p, L), seg_norm(p, L), nitems, j, pv);
+#pragma unroll
+  for (int m = 0; m < 24; ++m) pv[m] = rv[m] + be * pv[m];
+  SIO<P>::store(seg_ptr_w<P>(p, L), seg_norm(p, L), nitems, j, pv);
+}
+
+// out = (a + i b gamma_5) in, (a, b) per lattice from ep.e[l].a1/b1
+template <int P>
+__global__ void twist_kernel(Batch B, FieldRef out, FieldRef in, EpiSet ep, const int* mask) {
+  ITEM_PROLOGUE
+  if (!act) return;
+  typedef typename SIO<P>::real R;
+  R v[24];
+  SIO<P>::load(seg_ptr<P>(in, L), seg_norm(in, L), nitems, j, v);
+  twist_apply<R>(v, (R)ep.e[l].a1, (R)ep.e[l].b1);
+  SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, v);
+}
+
+template <int P>
+__global__ void zero_kernel(Batch B, FieldRef v, const int* mask) {
+  ITEM_PROLOGUE
+  if (!act) return;
+  typename SIO<P>::real a[24];
+#pragma unroll
+  for (int m = 0; m < 24; ++m) a[m] = 0;
+  SIO<P>::store(seg_ptr_w<P>(v, L), seg_norm(v, L), nitems, j, a);
+}
+
+// One CTA per global column: sum the column's partials over its lattice's blocks.
+__global__ void sum_partials_kernel(Batch B, const double* __restrict__ partial, double* __restrict__ out, int stride,
+                                    int slot) {
+  const int gc = blockIdx.x;
+  int l = -1, col = 0;
+  for (int k = 0; k < B.nlat; ++k)
+    if (gc >= B.lat[k].rhs_base && gc < B.lat[k].rhs_base + B.lat[k].ncol) {
+      l = k;
+      col = gc - B.lat[k].rhs_base;
+    }
+  __shared__ double s[256];
+  double acc = 0.0;
+  if (l >= 0)
+    for (int b = B.blk_begin[l] + threadIdx.x; b < B.blk_begin[l + 1]; b += blockDim.x)
+      acc += partial[(size_t)b * DL_MAXC + col];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && l >= 0) out[(size_t)slot * stride + gc] = s[0];
+}
+
+// alpha = rr / pAp for active columns
+#define SV(slot) S[(slot) * DL_NCMAX + gc]
+__global__ void cg_alpha_kernel(int ncols, double* S, int* active, int* flags) {
+  int gc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gc >= ncols || !active[gc]) return;
+  double pap = SV(DL_S_PAP);
+  if (!(pap > 0.0) || !isfinite(pap)) {
+    flags[gc] |= DL_FLAG_BREAKDOWN;
+    active[gc] = 0;
+    SV(DL_S_ALPHA) = 0.0;
+    return;
+  }
+  SV(DL_S_ALPHA) = SV(DL_S_RR) / pap;
+}
+
+// beta = rr_new / rr; convergence and reliable-update bookkeeping
+__global__ void cg_beta_kernel(int ncols, double* S, int* active, int* flags, int* iters, double tol2, double delta) {
+  int gc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gc >= ncols || !active[gc]) return;
+  double rrn = SV(DL_S_RRNEW);
+  iters[gc] += 1;
+  if (!isfinite(rrn)) {
+    flags[gc] |= DL_FLAG_BREAKDOWN;
+    active[gc] = 0;
+    SV(DL_S_BETA) = 0.0;
+    return;
+  }
+  SV(DL_S_BETA) = rrn / SV(DL_S_RR);
+  SV(DL_S_RR) = rrn;
+  double rn = sqrt(rrn);
+  if (rn > SV(DL_S_MAXR)) SV(DL_S_MAXR) = rn;
+  if (rrn <= tol2 * SV(DL_S_RR0)) {
+    flags[gc] |= DL_FLAG_CONVERGED;
+    active[gc] = 0;
+  } else if (delta > 0.0 && rn < delta * SV(DL_S_MAXR)) {
+    flags[gc] |= DL_FLAG_UPDATE;
+  }
+}
+#undef SV
+
+}  // namespace
+
+namespace dl {
+
+static int grid_of(Batch& B) { return blocks_for(B, 256); }
+
+#define DISPATCH_P(prec, CALL) \
+  switch (prec) {              \
+    case P64: { constexpr int PP = P64; CALL; } break; \
+    case P32: { constexpr int PP = P32; CALL; } break; \
+    case P16: { constexpr int PP = P16; CALL; } break; \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t copy(const Batch& Bin, int pd, int ps, FieldRef dst, FieldRef src, const int* mask, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+#define CP(a, b) if (pd == a && ps == b) { DL_COUNT(); copy_kernel<a, b><<<g, 256, 0, st>>>(B, dst, src, mask); return cudaGetLastError(); }
+  CP(P64, P64) CP(P64, P32) CP(P64, P16) CP(P32, P64) CP(P32, P32) CP(P32, P16) CP(P16, P64) CP(P16, P32) CP(P16, P16)
+#undef CP
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t accum(const Batch& Bin, int ph, int pl, FieldRef x, FieldRef y, const int* mask, int zero_y, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+#define AC(a, b) if (ph == a && pl == b) { DL_COUNT(); accum_kernel<a, b><<<g, 256, 0, st>>>(B, x, y, mask, zero_y); return cudaGetLastError(); }
+  AC(P64, P64) AC(P64, P32) AC(P64, P16) AC(P32, P32) AC(P32, P16)
+#undef AC
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t xmy_norm(const Batch& Bin, int prec, FieldRef r, FieldRef b, FieldRef a, const int* mask, double* partial,
+                     cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (xmy_norm_kernel<PP><<<g, 256, 0, st>>>(B, r, b, a, mask, partial)));
+  return cudaGetLastError();
+}
+
+cudaError_t norm2(const Batch& Bin, int prec, FieldRef v, const int* mask, double* partial, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (norm_kernel<PP><<<g, 256, 0, st>>>(B, v, mask, partial)));
+  return cudaGetLastError();
+}
+
+cudaError_t xpay(const Batch& Bin, int prec, FieldRef p, FieldRef r, const double* beta, const int* mask, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (xpay_kernel<PP><<<g, 256, 0, st>>>(B, p, r, beta, mask)));
+  return cudaGetLastError();
+}
+
+cudaError_t twist(const Batch& Bin, int prec, FieldRef out, FieldRef in, const EpiSet& ep, const int* mask, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (twist_kernel<PP><<<g, 256, 0, st>>>(B, out, in, ep, mask)));
+  return cudaGetLastError();
+}
+
+cudaError_t zero(const Batch& Bin, int prec, FieldRef v, const int* mask, cudaStream_t st) {
+  Batch B = Bin;
+  int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (zero_kernel<PP><<<g, 256, 0, st>>>(B, v, mask)));
+  return cudaGetLastError();
+}
+
+cudaError_t sum_partials(const Batch& Bin, const double* partial, double* out, int stride, int slot, int ncols_total,
+                         cudaStream_t st) {
+  Batch B = Bin;
+  grid_of(B);
+  if (ncols_total <= 0) return cudaSuccess;
+  DL_COUNT();
+  sum_partials_kernel<<<ncols_total, 256, 0, st>>>(B, partial, out, stride, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_alpha(int ncols, double* S, int* active, int* flags, cudaStream_t st) {
+  DL_COUNT();
+  cg_alpha_kernel<<<(ncols + 63) / 64, 64, 0, st>>>(ncols, S, active, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t cg_beta(int ncols, double* S, int* active, int* flags, int* iters, double tol2, double delta, cudaStream_t st) {
+  DL_COUNT();
+  cg_beta_kernel<<<(ncols + 63) / 64, 64, 0, st>>>(ncols, S, active, flags, iters, tol2, delta);
+  return cudaGetLastError();
+}
+
+}  // namespace dl

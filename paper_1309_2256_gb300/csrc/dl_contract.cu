@@ -1,0 +1,472 @@
+// Loop contractions (App. A, "Contraction kernels"): per site the colour-traced
+// Dirac outer product C_ab(x) = sum_c conj(xi_ac(x)) phi_bc(x) of the two
+// vectors of an estimator, the covariant-derivative bilinears, and the
+// momentum projection L(t, p) = sum_x exp(-i p.x) C(x, t) done as three
+// separable 1-D DFT passes (x, then y, then z) over the cube of integer
+// momenta, followed by the cut |n|^2 <= P.
+//
+// The symmetric derivative l^mu(x) = 1/4 [H(x) + H(x - mu)] with
+// H(x) = xi^+(x) U_mu(x) phi(x+mu) - xi^+(x+mu) U_mu(x)^+ phi(x) is the
+// four-term definition regrouped; the shift by mu becomes the phase
+// (1 + exp(-i p_mu)) for spatial mu and a sum of neighbouring time slices for t.
+#include "dl_internal.cuh"
+#include "dl_kernels.h"
+
+namespace {
+
+enum { MODE_STANDARD = 0, MODE_ONE_END = 1, MODE_GEN = 2, MODE_HPE = 3 };
+
+template <int P>
+__device__ __forceinline__ void load_d(const FieldRef& f, const LatDesc& L, long long nitems, long long j, double v[24]) {
+  typename SIO<P>::real a[24];
+  SIO<P>::load(seg_ptr<P>(f, L), seg_norm(f, L), nitems, j, a);
+#pragma unroll
+  for (int m = 0; m < 24; ++m) v[m] = (double)a[m];
+}
+
+// (xi, phi) of an estimator at one site from s (or w) and eta.
+template <int P, int MODE>
+__device__ __forceinline__ void make_pair(const FieldRef& s, const FieldRef& eta, const LatDesc& L, long long nitems,
+                                          long long j, double xi[24], double phi[24]) {
+  if (MODE == MODE_STANDARD || MODE == MODE_HPE) {
+    load_d<P>(eta, L, nitems, j, xi);
+    load_d<P>(s, L, nitems, j, phi);
+  } else if (MODE == MODE_ONE_END) {
+    load_d<P>(s, L, nitems, j, phi);
+#pragma unroll
+    for (int m = 0; m < 24; ++m) xi[m] = (m < 12) ? phi[m] : -phi[m];
+  } else {  // generalised: xi = g5 s, phi = g5 eta - 2 i kappa amu s
+    double e[24];
+    load_d<P>(s, L, nitems, j, xi);
+    load_d<P>(eta, L, nitems, j, e);
+    const double k2 = 2.0 * L.kappa * L.amu;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      double g = (m < 6) ? 1.0 : -1.0;
+      double sr = xi[2 * m], si = xi[2 * m + 1];
+      phi[2 * m] = g * e[2 * m] + k2 * si;
+      phi[2 * m + 1] = g * e[2 * m + 1] - k2 * sr;
+      xi[2 * m] = g * sr;
+      xi[2 * m + 1] = g * si;
+    }
+  }
+}
+
+template <int P, int MODE, bool DERIV>
+__global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e, FieldRef eta_o,
+                                      const double2* __restrict__ g64, double2* __restrict__ W) {
+  const LatDesc& L = B.lat[0];
+  const int npad = 1 << L.lognpad;
+  const long long V = 2LL * L.Vh;
+  const long long nfull = V * npad;
+  const long long nitems = (long long)L.Vh * npad;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nfull) return;
+  const int col = (int)(j & (npad - 1));
+  const int lex = (int)(j >> L.lognpad);
+  const int ncomp = DERIV ? 80 : 16;
+  if (col >= L.ncol) {
+    for (int c = 0; c < ncomp; ++c) W[(size_t)c * nfull + j] = make_double2(0.0, 0.0);
+    return;
+  }
+  int x = lex % L.X, r = lex / L.X;
+  int y = r % L.Y;
+  r /= L.Y;
+  int z = r % L.Z, t = r / L.Z;
+  const int p = (x + y + z + t) & 1;
+  const long long jj = ((long long)(lex >> 1) << L.lognpad) + col;
+  double xi[24], phi[24];
+  make_pair<P, MODE>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, jj, xi, phi);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double xr = xi[2 * (3 * a + c)], xim = xi[2 * (3 * a + c) + 1];
+        double pr = phi[2 * (3 * b + c)], pim = phi[2 * (3 * b + c) + 1];
+        re += xr * pr + xim * pim;
+        im += xr * pim - xim * pr;
+      }
+      W[(size_t)(4 * a + b) * nfull + j] = make_double2(re, im);
+    }
+  if (DERIV) {
+    for (int mu = 0; mu < 4; ++mu) {
+      int xn = x, yn = y, zn = z, tn = t;
+      double bc = 1.0;
+      if (mu == 0) xn = (x + 1 == L.X) ? 0 : x + 1;
+      if (mu == 1) yn = (y + 1 == L.Y) ? 0 : y + 1;
+      if (mu == 2) zn = (z + 1 == L.Z) ? 0 : z + 1;
+      if (mu == 3) {
+        tn = (t + 1 == L.T) ? 0 : t + 1;
+        if (t + 1 == L.T) bc = L.tbc;
+      }
+      const int lexn = lex_of(L, xn, yn, zn, tn);
+      const long long jn = ((long long)(lexn >> 1) << L.lognpad) + col;
+      double xif[24], phif[24];
+      make_pair<P, MODE>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, jn, xif, phif);
+#pragma unroll
+      for (int m = 0; m < 24; ++m) {
+        xif[m] *= bc;
+        phif[m] *= bc;
+      }
+      // U_mu(x), parity p, checkerboard index lex >> 1
+      double u[18];
+      const double2* gl = g64 + (size_t)((p * 4 + mu) * 9) * L.Vh + (lex >> 1);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        double2 c = gl[(size_t)k * L.Vh];
+        u[2 * k] = c.x;
+        u[2 * k + 1] = c.y;
+      }
+      double up[24], udp[24];  // U phi(x+mu), U^+ phi(x)
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          double r1 = 0, i1 = 0, r2 = 0, i2 = 0;
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            double ur = u[2 * (3 * a + b)], ui = u[2 * (3 * a + b) + 1];
+            double vr = phif[2 * (3 * s + b)], vi = phif[2 * (3 * s + b) + 1];
+            r1 += ur * vr - ui * vi;
+            i1 += ur * vi + ui * vr;
+            double wr = u[2 * (3 * b + a)], wi = -u[2 * (3 * b + a) + 1];
+            double qr = phi[2 * (3 * s + b)], qi = phi[2 * (3 * s + b) + 1];
+            r2 += wr * qr - wi * qi;
+            i2 += wr * qi + wi * qr;
+          }
+          up[2 * (3 * s + a)] = r1;
+          up[2 * (3 * s + a) + 1] = i1;
+          udp[2 * (3 * s + a)] = r2;
+          udp[2 * (3 * s + a) + 1] = i2;
+        }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          double re = 0.0, im = 0.0;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            double xr = xi[2 * (3 * a + c)], xim = xi[2 * (3 * a + c) + 1];
+            double pr = up[2 * (3 * b + c)], pim = up[2 * (3 * b + c) + 1];
+            re += xr * pr + xim * pim;
+            im += xr * pim - xim * pr;
+            double fr = xif[2 * (3 * a + c)], fim = xif[2 * (3 * a + c) + 1];
+            double qr = udp[2 * (3 * b + c)], qim = udp[2 * (3 * b + c) + 1];
+            re -= fr * qr + fim * qim;
+            im -= fr * qim - fim * qr;
+          }
+          W[(size_t)(16 * (mu + 1) + 4 * a + b) * nfull + j] = make_double2(re, im);
+        }
+    }
+  }
+}
+
+__global__ void phase_kernel(int len, double2* ph) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  double s, c;
+  sincospi(2.0 * (double)q / (double)len, &s, &c);
+  ph[q] = make_double2(c, -s);  // exp(-2 pi i q / len)
+}
+
+// out[b][k][s] = sum_j in[b][j][s] exp(-2 pi i (k - m) j / len)
+__global__ void dft_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long nb, int len,
+                           long long stride, int m, const double2* __restrict__ ph) {
+  const int nk = 2 * m + 1;
+  const long long tot = nb * nk * stride;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long s = idx % stride;
+    long long r = idx / stride;
+    int k = (int)(r % nk);
+    long long b = r / nk;
+    int n = k - m;
+    n = ((n % len) + len) % len;
+    const double2* src = in + (b * len) * stride + s;
+    double re = 0.0, im = 0.0;
+    int q = 0;
+    for (int jx = 0; jx < len; ++jx) {
+      double2 v = src[(long long)jx * stride];
+      double2 w = ph[q];
+      re += v.x * w.x - v.y * w.y;
+      im += v.x * w.y + v.y * w.x;
+      q += n;
+      if (q >= len) q -= len;
+    }
+    out[idx] = make_double2(re, im);
+  }
+}
+
+// out[col][t][ip][d][ab] (+)= pre * finalised G3
+__global__ void finalize_kernel(LatDesc L, int npad, int nd, int np, const int* __restrict__ mom, int mx, int my, int mz,
+                                const double2* __restrict__ G3,
+                                double pre_re, double pre_im, double2* out, int accumulate) {
+  const long long tot = (long long)L.ncol * L.T * np * nd * 16;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tot) return;
+  int ab = (int)(idx % 16);
+  long long r = idx / 16;
+  int d = (int)(r % nd);
+  r /= nd;
+  int ip = (int)(r % np);
+  r /= np;
+  int t = (int)(r % L.T);
+  int col = (int)(r / L.T);
+  int nx = mom[3 * ip], ny = mom[3 * ip + 1], nz = mom[3 * ip + 2];
+  const int NX = 2 * mx + 1, NY = 2 * my + 1, NZ = 2 * mz + 1;
+  const long long cube = (long long)NZ * NY * NX * npad;
+  auto g = [&](int comp, int tt) -> double2 {
+    long long o = ((long long)comp * L.T + tt) * cube + (((long long)(nz + mz) * NY + (ny + my)) * NX + (nx + mx)) * npad + col;
+    return G3[o];
+  };
+  double2 v;
+  if (d == 0) {
+    v = g(ab, t);
+  } else if (d < 4) {
+    double2 h = g(16 * d + ab, t);
+    int nmu = (d == 1) ? nx : (d == 2 ? ny : nz);
+    int lmu = (d == 1) ? L.X : (d == 2 ? L.Y : L.Z);
+    double s, c;
+    sincospi(2.0 * (double)nmu / (double)lmu, &s, &c);
+    double fr = 0.25 * (1.0 + c), fi = -0.25 * s;  // (1 + exp(-i p_mu)) / 4
+    v = make_double2(fr * h.x - fi * h.y, fr * h.y + fi * h.x);
+  } else {
+    double2 h0 = g(64 + ab, t), h1 = g(64 + ab, (t == 0) ? L.T - 1 : t - 1);
+    v = make_double2(0.25 * (h0.x + h1.x), 0.25 * (h0.y + h1.y));
+  }
+  double2 res = make_double2(pre_re * v.x - pre_im * v.y, pre_re * v.y + pre_im * v.x);
+  if (accumulate) {
+    double2 o = out[idx];
+    res.x += o.x;
+    res.y += o.y;
+  }
+  out[idx] = res;
+}
+
+// Exact hopping-parameter-expansion terms for local insertions at one site:
+// E = B + kappa^2 B S B with S = sum_mu [(1 - g_mu) B (1 + g_mu) + (1 + g_mu) B (1 - g_mu)],
+// colour trace 3; written in the bilinear convention C_ab = 3 E_ba.
+struct c4 {
+  double r[4][4], i[4][4];
+};
+__device__ void mm4(const c4& a, const c4& b, c4& o) {
+  for (int x = 0; x < 4; ++x)
+    for (int y = 0; y < 4; ++y) {
+      double re = 0, im = 0;
+      for (int k = 0; k < 4; ++k) {
+        re += a.r[x][k] * b.r[k][y] - a.i[x][k] * b.i[k][y];
+        im += a.r[x][k] * b.i[k][y] + a.i[x][k] * b.r[k][y];
+      }
+      o.r[x][y] = re;
+      o.i[x][y] = im;
+    }
+}
+__global__ void hpe_exact_kernel(double kappa, double amu, int flavour, double2* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // chiral gammas: g_k = [[0, -i s_k], [i s_k, 0]], g_t = [[0, 1], [1, 0]]
+  c4 g[4];
+  for (int mu = 0; mu < 4; ++mu)
+    for (int x = 0; x < 4; ++x)
+      for (int y = 0; y < 4; ++y) g[mu].r[x][y] = g[mu].i[x][y] = 0.0;
+  // sigma_1 = [[0,1],[1,0]], sigma_2 = [[0,-i],[i,0]], sigma_3 = diag(1,-1)
+  // -i s_1 = [[0,-i],[-i,0]]
+  g[0].i[0][3] = -1; g[0].i[1][2] = -1; g[0].i[2][1] = 1; g[0].i[3][0] = 1;
+  // -i s_2 = [[0,-1],[1,0]], i s_2 = [[0,1],[-1,0]]
+  g[1].r[0][3] = -1; g[1].r[1][2] = 1; g[1].r[2][1] = 1; g[1].r[3][0] = -1;
+  // -i s_3 = diag(-i, i), i s_3 = diag(i, -i)
+  g[2].i[0][2] = -1; g[2].i[1][3] = 1; g[2].i[2][0] = 1; g[2].i[3][1] = -1;
+  g[3].r[0][2] = 1; g[3].r[1][3] = 1; g[3].r[2][0] = 1; g[3].r[3][1] = 1;
+  // B = (1 + i w g5)^-1 = (1 - i w g5) / (1 + w^2), w = 2 kappa amu f
+  const double w = 2.0 * kappa * amu * flavour, n = 1.0 / (1.0 + w * w);
+  c4 Bm, S, T1, T2, P1, P2;
+  for (int x = 0; x < 4; ++x)
+    for (int y = 0; y < 4; ++y) {
+      Bm.r[x][y] = (x == y) ? n : 0.0;
+      Bm.i[x][y] = (x == y) ? -w * n * (x < 2 ? 1.0 : -1.0) : 0.0;
+      S.r[x][y] = S.i[x][y] = 0.0;
+    }
+  for (int mu = 0; mu < 4; ++mu)
+    for (int sg = -1; sg <= 1; sg += 2) {
+      for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+          double id = (x == y) ? 1.0 : 0.0;
+          P1.r[x][y] = id - sg * g[mu].r[x][y];
+          P1.i[x][y] = -sg * g[mu].i[x][y];
+          P2.r[x][y] = id + sg * g[mu].r[x][y];
+          P2.i[x][y] = sg * g[mu].i[x][y];
+        }
+      mm4(P1, Bm, T1);
+      mm4(T1, P2, T2);
+      for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+          S.r[x][y] += T2.r[x][y];
+          S.i[x][y] += T2.i[x][y];
+        }
+    }
+  mm4(Bm, S, T1);
+  mm4(T1, Bm, T2);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double er = Bm.r[b][a] + kappa * kappa * T2.r[b][a];
+      double ei = Bm.i[b][a] + kappa * kappa * T2.i[b][a];
+      out[4 * a + b] = make_double2(3.0 * er, 3.0 * ei);
+    }
+}
+
+__global__ void add_exact_kernel(LatDesc L, int np, int nd, int ip0, const double2* __restrict__ ex, double scale,
+                                 double2* out) {
+  long long tot = (long long)L.ncol * L.T * 16;
+  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= tot) return;
+  int ab = (int)(idx % 16);
+  long long r = idx / 16;
+  int t = (int)(r % L.T);
+  int col = (int)(r / L.T);
+  long long o = ((((long long)col * L.T + t) * np + ip0) * nd + 0) * 16 + ab;
+  out[o].x += scale * ex[ab].x;
+  out[o].y += scale * ex[ab].y;
+}
+
+// acc[k] += sign * sum_col (blk[col][k] - sub[col][k])  (sub may be null)
+__global__ void col_accumulate_kernel(const double2* __restrict__ blk, const double2* __restrict__ sub, int ncol,
+                                      long long per_col, double sign, double2* acc) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= per_col) return;
+  double re = 0.0, im = 0.0;
+  for (int col = 0; col < ncol; ++col) {
+    double2 v = blk[(long long)col * per_col + k];
+    re += v.x;
+    im += v.y;
+    if (sub) {
+      double2 w = sub[(long long)col * per_col + k];
+      re -= w.x;
+      im -= w.y;
+    }
+  }
+  acc[k].x += sign * re;
+  acc[k].y += sign * im;
+}
+
+// Per-column scalar observables at zero momentum summed over t:
+//   sigma = sum_ab (i g5)_ab L1_ab,   axial = sum_ab (g_z g5)_ab L2_ab
+// with g_z g5 = [[0, i s3], [i s3, 0]] in the chiral basis.
+__global__ void observables_kernel(const double2* __restrict__ l1, const double2* __restrict__ l2, int ncol, int T, int np,
+                                   int nd, int ip0, double* obs) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  double sr = 0, si = 0, ar = 0, ai = 0;
+  for (int t = 0; t < T; ++t) {
+    long long o = ((((long long)col * T + t) * np + ip0) * nd) * 16;
+    const double2* a = l1 + o;
+    const double2* b = l2 + o;
+    // i g5 = diag(i, i, -i, -i): i * (C00 + C11 - C22 - C33)
+    double dr = a[0].x + a[5].x - a[10].x - a[15].x, di = a[0].y + a[5].y - a[10].y - a[15].y;
+    sr += -di;
+    si += dr;
+    // (0,2) = i, (1,3) = -i, (2,0) = i, (3,1) = -i
+    double er = b[2].x - b[7].x + b[8].x - b[13].x, ei = b[2].y - b[7].y + b[8].y - b[13].y;
+    ar += -ei;
+    ai += er;
+  }
+  obs[4 * col + 0] = sr;
+  obs[4 * col + 1] = si;
+  obs[4 * col + 2] = ar;
+  obs[4 * col + 3] = ai;
+}
+
+// out = a * x + b * y
+__global__ void combine_kernel(const double2* x, const double2* y, double a, double b, long long n, double2* out) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = make_double2(a * x[k].x + b * y[k].x, a * x[k].y + b * y[k].y);
+}
+
+}  // namespace
+
+namespace dl {
+
+cudaError_t col_accumulate(const double2* blk, const double2* sub, int ncol, long long per_col, double sign, double2* acc,
+                           cudaStream_t st) {
+  if (per_col <= 0) return cudaSuccess;
+  DL_COUNT();
+  col_accumulate_kernel<<<(int)((per_col + 255) / 256), 256, 0, st>>>(blk, sub, ncol, per_col, sign, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t observables(const double2* l1, const double2* l2, int ncol, int T, int np, int nd, int ip0, double* obs,
+                        cudaStream_t st) {
+  DL_COUNT();
+  observables_kernel<<<(ncol + 31) / 32, 32, 0, st>>>(l1, l2, ncol, T, np, nd, ip0, obs);
+  return cudaGetLastError();
+}
+
+cudaError_t combine(const double2* x, const double2* y, double a, double b, long long n, double2* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  DL_COUNT();
+  combine_kernel<<<(int)((n + 255) / 256), 256, 0, st>>>(x, y, a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+                           FieldRef eta_o, const void* g64, double2* W, cudaStream_t st) {
+  const LatDesc& L = B.lat[0];
+  long long nfull = (2LL * L.Vh) << L.lognpad;
+  int g = (int)((nfull + 127) / 128);
+  const double2* gg = (const double2*)g64;
+#define CS(PR, MD)                                                                                          \
+  if (prec == PR && mode == MD) {                                                                           \
+    DL_COUNT();                                                                                             \
+    if (with_deriv) contract_sites_kernel<PR, MD, true><<<g, 128, 0, st>>>(B, s_e, s_o, eta_e, eta_o, gg, W);  \
+    else contract_sites_kernel<PR, MD, false><<<g, 128, 0, st>>>(B, s_e, s_o, eta_e, eta_o, gg, W);          \
+    return cudaGetLastError();                                                                              \
+  }
+  CS(P64, 0) CS(P64, 1) CS(P64, 2) CS(P64, 3) CS(P32, 0) CS(P32, 1) CS(P32, 2) CS(P32, 3)
+#undef CS
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
+                     cudaStream_t st) {
+  DL_COUNT();
+  phase_kernel<<<(len + 63) / 64, 64, 0, st>>>(len, phase);
+  long long tot = nb * (2 * m + 1) * stride;
+  long long g = (tot + 255) / 256;
+  if (g > 152LL * 64) g = 152LL * 64;
+  if (g < 1) g = 1;
+  DL_COUNT();
+  dft_kernel<<<(int)g, 256, 0, st>>>(in, out, nb, len, stride, m, phase);
+  return cudaGetLastError();
+}
+
+cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
+                              const double2* G3, double pre_re, double pre_im, double2* out, int accumulate,
+                              cudaStream_t st) {
+  const LatDesc& L = B.lat[0];
+  int nd = with_deriv ? 5 : 1;
+  long long tot = (long long)L.ncol * L.T * np * nd * 16;
+  if (tot == 0) return cudaSuccess;
+  DL_COUNT();
+  finalize_kernel<<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz, G3, pre_re,
+                                                           pre_im, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t hpe_exact(double kappa, double amu, int flavour, double2* out16, cudaStream_t st) {
+  DL_COUNT();
+  hpe_exact_kernel<<<1, 32, 0, st>>>(kappa, amu, flavour, out16);
+  return cudaGetLastError();
+}
+
+cudaError_t add_exact_p0(const Batch& B, int np, int nd, int ip0, const double2* exact16, double scale, double2* out,
+                         cudaStream_t st) {
+  const LatDesc& L = B.lat[0];
+  long long tot = (long long)L.ncol * L.T * 16;
+  DL_COUNT();
+  add_exact_kernel<<<(int)((tot + 255) / 256), 256, 0, st>>>(L, np, nd, ip0, exact16, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dl

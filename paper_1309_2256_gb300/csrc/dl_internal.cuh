@@ -1,0 +1,441 @@
+// Internal definitions shared by the discloop CUDA translation units.
+//
+// Device layouts (all 16-byte chunks so that every load/store is 128-bit):
+//   spinor parity field, per lattice: chunk k of item j at  base + k*(Vh*npad) + j,
+//     item j = site*npad + column, npad = 2^lognpad >= active columns.
+//     F64: 12 chunks of double2 (one complex each, m = 3*spin + colour)
+//     F32:  6 chunks of float4  (complex 2k, 2k+1)
+//     F16:  3 chunks of uint4   (8 halves = complex 4k..4k+3) + float norm[item]
+//           (values are stored divided by the item's max |re|,|im|)
+//   gauge field, per lattice: chunk k of link (parity p, mu, site i) at
+//     base + ((p*4 + mu)*GK + k)*Vh + i
+//     F64 recon 18: 9 double2 (row-major complex entries)
+//     F32 recon 12: 3 float4  (rows 0 and 1), row 2 = conj(row0 x row1)
+//     F32 recon  8: 2 float4  (a1, a2, b0, arg a0, arg c0)
+//     F16 recon 12: 3 uint2   (rows 0 and 1 as halves)
+//     F16 recon  8: 1 uint4   (a1, a2, b0, arg a0 / pi, arg c0 / pi)
+// Several lattices can share one launch ("batch"): lattice l owns blocks
+// [blk_begin_l, blk_begin_{l+1}) and its own segment of every field.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#define DL_MAX_LAT 8
+#define DL_MAXC 32  // max columns (right-hand sides) per lattice segment
+
+enum { P64 = 0, P32 = 1, P16 = 2 };
+
+// ---------------------------------------------------------------- batch
+struct LatDesc {
+  int X, Y, Z, T;
+  int Vh;            // sites per parity
+  int lognpad;       // columns padded to 2^lognpad
+  int ncol;          // active columns
+  int rhs_base;      // global column index of column 0
+  long long item_off;   // item offset of this lattice in a parity field
+  long long gsite_off;  // parity-site offset of this lattice in the gauge arrays
+  double tbc;        // time-boundary factor
+  double kappa, amu;
+};
+
+struct Batch {
+  int nlat;
+  int blk_begin[DL_MAX_LAT + 1];
+  LatDesc lat[DL_MAX_LAT];
+};
+
+__device__ __forceinline__ int find_lat(const Batch& B, int blk) {
+  int l = 0;
+#pragma unroll 1
+  for (int k = 1; k < B.nlat; ++k)
+    if (blk >= B.blk_begin[k]) l = k;
+  return l;
+}
+
+// Coordinates of checkerboard site i of parity p.
+__device__ __forceinline__ void cb_coords(const LatDesc& L, int i, int p, int& x, int& y, int& z, int& t) {
+  int full = 2 * i;
+  int xh = full % L.X;
+  int rest = full / L.X;
+  y = rest % L.Y;
+  rest /= L.Y;
+  z = rest % L.Z;
+  t = rest / L.Z;
+  x = xh + ((y + z + t + p) & 1);
+}
+
+__device__ __forceinline__ int lex_of(const LatDesc& L, int x, int y, int z, int t) {
+  return x + L.X * (y + L.Y * (z + L.Z * t));
+}
+
+// ---------------------------------------------------------------- spinor IO
+template <int P> struct SIO;
+
+template <> struct SIO<P64> {
+  typedef double real;
+  static constexpr int K = 12;
+  __device__ static __forceinline__ void load(const void* b, const float*, long long st, long long j, double v[24]) {
+    const double2* p = (const double2*)b;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 c = __ldg(p + k * st + j);
+      v[2 * k] = c.x;
+      v[2 * k + 1] = c.y;
+    }
+  }
+  __device__ static __forceinline__ void store(void* b, float*, long long st, long long j, const double v[24]) {
+    double2* p = (double2*)b;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k * st + j] = make_double2(v[2 * k], v[2 * k + 1]);
+  }
+};
+
+template <> struct SIO<P32> {
+  typedef float real;
+  static constexpr int K = 6;
+  __device__ static __forceinline__ void load(const void* b, const float*, long long st, long long j, float v[24]) {
+    const float4* p = (const float4*)b;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 c = __ldg(p + k * st + j);
+      v[4 * k] = c.x;
+      v[4 * k + 1] = c.y;
+      v[4 * k + 2] = c.z;
+      v[4 * k + 3] = c.w;
+    }
+  }
+  __device__ static __forceinline__ void store(void* b, float*, long long st, long long j, const float v[24]) {
+    float4* p = (float4*)b;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k * st + j] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  }
+};
+
+template <> struct SIO<P16> {
+  typedef float real;
+  static constexpr int K = 3;
+  __device__ static __forceinline__ void load(const void* b, const float* nrm, long long st, long long j, float v[24]) {
+    const uint4* p = (const uint4*)b;
+    float s = __ldg(nrm + j);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c = __ldg(p + k * st + j);
+      const __half2* h = reinterpret_cast<const __half2*>(&c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 f = __half22float2(h[q]);
+        v[8 * k + 2 * q] = f.x * s;
+        v[8 * k + 2 * q + 1] = f.y * s;
+      }
+    }
+  }
+  __device__ static __forceinline__ void store(void* b, float* nrm, long long st, long long j, const float v[24]) {
+    uint4* p = (uint4*)b;
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < 24; ++q) m = fmaxf(m, fabsf(v[q]));
+    float inv = m > 0.f ? 1.0f / m : 0.f;
+    nrm[j] = m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c;
+      __half2* h = reinterpret_cast<__half2*>(&c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(v[8 * k + 2 * q] * inv, v[8 * k + 2 * q + 1] * inv);
+      p[k * st + j] = c;
+    }
+  }
+};
+
+// A parity field of the whole batch: data pointer to chunk 0 of the first
+// lattice; lattice l's segment starts at chunk K*item_off_l (norms at item_off_l).
+struct FieldRef {
+  void* data;
+  float* norm;
+};
+
+template <int P>
+__device__ __forceinline__ const void* seg_ptr(const FieldRef& f, const LatDesc& L) {
+  constexpr int bytes = 16;
+  return (const char*)f.data + (size_t)SIO<P>::K * bytes * (size_t)L.item_off;
+}
+template <int P>
+__device__ __forceinline__ void* seg_ptr_w(const FieldRef& f, const LatDesc& L) {
+  return (char*)f.data + (size_t)SIO<P>::K * 16 * (size_t)L.item_off;
+}
+__device__ __forceinline__ float* seg_norm(const FieldRef& f, const LatDesc& L) {
+  return f.norm ? f.norm + L.item_off : nullptr;
+}
+
+// ---------------------------------------------------------------- gauge IO
+enum { G64R18 = 0, G32R12 = 1, G32R8 = 2, G16R12 = 3, G16R8 = 4 };
+
+template <int G> struct GIO;
+
+template <typename R>
+__device__ __forceinline__ void recon12(R u[18]) {
+  // row 2 = conj(row0 x row1)
+  R a0r = u[0], a0i = u[1], a1r = u[2], a1i = u[3], a2r = u[4], a2i = u[5];
+  R b0r = u[6], b0i = u[7], b1r = u[8], b1i = u[9], b2r = u[10], b2i = u[11];
+  u[12] = (a1r * b2r - a1i * b2i) - (a2r * b1r - a2i * b1i);
+  u[13] = -((a1r * b2i + a1i * b2r) - (a2r * b1i + a2i * b1r));
+  u[14] = (a2r * b0r - a2i * b0i) - (a0r * b2r - a0i * b2i);
+  u[15] = -((a2r * b0i + a2i * b0r) - (a0r * b2i + a0i * b2r));
+  u[16] = (a0r * b1r - a0i * b1i) - (a1r * b0r - a1i * b0i);
+  u[17] = -((a0r * b1i + a0i * b1r) - (a1r * b0i + a1i * b0r));
+}
+
+// Rebuild an SU(3) matrix from (a1, a2, b0, arg a0, arg c0) using unitarity
+// (unit first row and column) and U^dagger = adj(U) for det U = 1.
+__device__ __forceinline__ void recon8(float a1r, float a1i, float a2r, float a2i, float b0r, float b0i, float ta,
+                                       float tc, float u[18]) {
+  float n = a1r * a1r + a1i * a1i + a2r * a2r + a2i * a2i;
+  float ma0 = sqrtf(fmaxf(0.f, 1.f - n));
+  float sa, ca, sc, cc;
+  sincosf(ta, &sa, &ca);
+  sincosf(tc, &sc, &cc);
+  float a0r = ma0 * ca, a0i = ma0 * sa;
+  float mc0 = sqrtf(fmaxf(0.f, n - (b0r * b0r + b0i * b0i)));  // 1 - |a0|^2 - |b0|^2
+  float c0r = mc0 * cc, c0i = mc0 * sc;
+  float in = 1.f / n;
+  // conj helpers: x* = (xr, -xi)
+  // b1 = -(a0* a1 b0 + a2* c0*) / n
+  float t1r = (a0r * a1r + a0i * a1i), t1i = (a0r * a1i - a0i * a1r);  // a0* a1
+  float t2r = t1r * b0r - t1i * b0i, t2i = t1r * b0i + t1i * b0r;      // a0* a1 b0
+  float t3r = a2r * c0r - a2i * c0i, t3i = -(a2r * c0i + a2i * c0r);   // a2* c0* = conj(a2 c0)
+  float b1r = -(t2r + t3r) * in, b1i = -(t2i + t3i) * in;
+  // b2 = (a1* c0* - a0* a2 b0) / n
+  float s1r = a1r * c0r - a1i * c0i, s1i = -(a1r * c0i + a1i * c0r);  // conj(a1 c0)
+  float s2r = (a0r * a2r + a0i * a2i), s2i = (a0r * a2i - a0i * a2r);  // a0* a2
+  float s3r = s2r * b0r - s2i * b0i, s3i = s2r * b0i + s2i * b0r;
+  float b2r = (s1r - s3r) * in, b2i = (s1i - s3i) * in;
+  // c1 = (a2* b0* - a0* a1 c0) / n
+  float q1r = a2r * b0r - a2i * b0i, q1i = -(a2r * b0i + a2i * b0r);  // conj(a2 b0)
+  float q2r = t1r * c0r - t1i * c0i, q2i = t1r * c0i + t1i * c0r;      // a0* a1 c0
+  float c1r = (q1r - q2r) * in, c1i = (q1i - q2i) * in;
+  // c2 = -(a0* a2 c0 + a1* b0*) / n
+  float w1r = s2r * c0r - s2i * c0i, w1i = s2r * c0i + s2i * c0r;      // a0* a2 c0
+  float w2r = a1r * b0r - a1i * b0i, w2i = -(a1r * b0i + a1i * b0r);  // conj(a1 b0)
+  float c2r = -(w1r + w2r) * in, c2i = -(w1i + w2i) * in;
+  u[0] = a0r; u[1] = a0i; u[2] = a1r; u[3] = a1i; u[4] = a2r; u[5] = a2i;
+  u[6] = b0r; u[7] = b0i; u[8] = b1r; u[9] = b1i; u[10] = b2r; u[11] = b2i;
+  u[12] = c0r; u[13] = c0i; u[14] = c1r; u[15] = c1i; u[16] = c2r; u[17] = c2i;
+}
+
+template <> struct GIO<G64R18> {
+  typedef double real;
+  static constexpr int GK = 9;
+  typedef double2 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, double u[18]) {
+    const double2* g = (const double2*)b + (size_t)((p * 4 + mu) * 9) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 c = __ldg(g + (size_t)k * Vh);
+      u[2 * k] = c.x;
+      u[2 * k + 1] = c.y;
+    }
+  }
+};
+template <> struct GIO<G32R12> {
+  typedef float real;
+  static constexpr int GK = 3;
+  typedef float4 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
+    const float4* g = (const float4*)b + (size_t)((p * 4 + mu) * 3) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 c = __ldg(g + (size_t)k * Vh);
+      u[4 * k] = c.x; u[4 * k + 1] = c.y; u[4 * k + 2] = c.z; u[4 * k + 3] = c.w;
+    }
+    recon12(u);
+  }
+};
+template <> struct GIO<G32R8> {
+  typedef float real;
+  static constexpr int GK = 2;
+  typedef float4 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
+    const float4* g = (const float4*)b + (size_t)((p * 4 + mu) * 2) * Vh + i;
+    float4 c0 = __ldg(g), c1 = __ldg(g + Vh);
+    recon8(c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, u);
+  }
+};
+template <> struct GIO<G16R12> {
+  typedef float real;
+  static constexpr int GK = 3;
+  typedef uint2 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
+    const uint2* g = (const uint2*)b + (size_t)((p * 4 + mu) * 3) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint2 c = __ldg(g + (size_t)k * Vh);
+      const __half2* h = reinterpret_cast<const __half2*>(&c);
+      float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
+      u[4 * k] = f0.x; u[4 * k + 1] = f0.y; u[4 * k + 2] = f1.x; u[4 * k + 3] = f1.y;
+    }
+    recon12(u);
+  }
+};
+template <> struct GIO<G16R8> {
+  typedef float real;
+  static constexpr int GK = 1;
+  typedef uint4 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
+    const uint4* g = (const uint4*)b + (size_t)((p * 4 + mu)) * Vh + i;
+    uint4 c = __ldg(g);
+    const __half2* h = reinterpret_cast<const __half2*>(&c);
+    float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]), f2 = __half22float2(h[2]), f3 = __half22float2(h[3]);
+    const float pi = 3.14159265358979f;
+    recon8(f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x * pi, f3.y * pi, u);
+  }
+};
+
+template <int G>
+__device__ __forceinline__ const void* gauge_seg(const void* base, const LatDesc& L) {
+  return (const char*)base + (size_t)sizeof(typename GIO<G>::chunk) * GIO<G>::GK * 8 * (size_t)L.gsite_off;
+}
+
+// ---------------------------------------------------------------- spin algebra
+// Hop contribution along mu with projector (1 + s gamma_mu), colour matrix u
+// (adjoint if DAGU):  acc += (1 + s gamma_mu) U psi.
+// With G_mu the upper-right block of gamma_mu (G_k = -i sigma_k, G_t = 1):
+//   h = psi_up + s G psi_dn,  chi = U h,  acc_up += chi,  acc_dn += s G^dagger chi.
+template <typename R, bool DAGU, int mu>
+__device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18], R s) {
+  R h[12];  // [spin 0..1][colour][re,im]
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R u0r = v[2 * c], u0i = v[2 * c + 1];            // spin 0
+    R u1r = v[6 + 2 * c], u1i = v[6 + 2 * c + 1];    // spin 1
+    R d2r = v[12 + 2 * c], d2i = v[12 + 2 * c + 1];  // spin 2
+    R d3r = v[18 + 2 * c], d3i = v[18 + 2 * c + 1];  // spin 3
+    R h0r, h0i, h1r, h1i;
+    if (mu == 0) {        // G = [[0,-i],[-i,0]]: (G d)_0 = -i d3, (G d)_1 = -i d2
+      h0r = u0r + s * d3i; h0i = u0i - s * d3r;
+      h1r = u1r + s * d2i; h1i = u1i - s * d2r;
+    } else if (mu == 1) { // G = [[0,-1],[1,0]]: (G d)_0 = -d3, (G d)_1 = d2
+      h0r = u0r - s * d3r; h0i = u0i - s * d3i;
+      h1r = u1r + s * d2r; h1i = u1i + s * d2i;
+    } else if (mu == 2) { // G = diag(-i, i): (G d)_0 = -i d2, (G d)_1 = i d3
+      h0r = u0r + s * d2i; h0i = u0i - s * d2r;
+      h1r = u1r - s * d3i; h1i = u1i + s * d3r;
+    } else {              // G = 1
+      h0r = u0r + s * d2r; h0i = u0i + s * d2i;
+      h1r = u1r + s * d3r; h1i = u1i + s * d3i;
+    }
+    h[2 * c] = h0r; h[2 * c + 1] = h0i;
+    h[6 + 2 * c] = h1r; h[6 + 2 * c + 1] = h1i;
+  }
+  R chi[12];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      R re = 0, im = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R ur, ui;
+        if (DAGU) { ur = u[2 * (3 * b + a)]; ui = -u[2 * (3 * b + a) + 1]; }
+        else { ur = u[2 * (3 * a + b)]; ui = u[2 * (3 * a + b) + 1]; }
+        R hr = h[6 * sp + 2 * b], hi = h[6 * sp + 2 * b + 1];
+        re += ur * hr - ui * hi;
+        im += ur * hi + ui * hr;
+      }
+      chi[6 * sp + 2 * a] = re;
+      chi[6 * sp + 2 * a + 1] = im;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R c0r = chi[2 * c], c0i = chi[2 * c + 1], c1r = chi[6 + 2 * c], c1i = chi[6 + 2 * c + 1];
+    acc[2 * c] += c0r; acc[2 * c + 1] += c0i;
+    acc[6 + 2 * c] += c1r; acc[6 + 2 * c + 1] += c1i;
+    R l2r, l2i, l3r, l3i;  // G^dagger chi
+    if (mu == 0) {        // G^+ = [[0,i],[i,0]]: (G^+ c)_0 = i c1, (G^+ c)_1 = i c0
+      l2r = -c1i; l2i = c1r; l3r = -c0i; l3i = c0r;
+    } else if (mu == 1) { // G^+ = [[0,1],[-1,0]]: (G^+ c)_0 = c1, (G^+ c)_1 = -c0
+      l2r = c1r; l2i = c1i; l3r = -c0r; l3i = -c0i;
+    } else if (mu == 2) { // G^+ = diag(i, -i)
+      l2r = -c0i; l2i = c0r; l3r = c1i; l3i = -c1r;
+    } else {
+      l2r = c0r; l2i = c0i; l3r = c1r; l3i = c1i;
+    }
+    acc[12 + 2 * c] += s * l2r; acc[12 + 2 * c + 1] += s * l2i;
+    acc[18 + 2 * c] += s * l3r; acc[18 + 2 * c + 1] += s * l3i;
+  }
+}
+
+// (a + i b gamma_5) v, gamma_5 = diag(1,1,-1,-1)
+template <typename R>
+__device__ __forceinline__ void twist_apply(R v[24], R a, R b) {
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    R bb = (m < 6) ? b : -b;
+    R re = v[2 * m], im = v[2 * m + 1];
+    v[2 * m] = a * re - bb * im;
+    v[2 * m + 1] = a * im + bb * re;
+  }
+}
+
+// Per-column block reduction (deterministic).  Each thread contributes val for
+// column col = (its item index) & (npad-1); blockDim.x is a multiple of 32 and
+// npad <= 32.  Writes partial[blockIdx.x * DL_MAXC + col] for col < npad.
+__device__ __forceinline__ void block_reduce_cols(double val, int npad, double* partial) {
+  __shared__ double sred[32][DL_MAXC];
+  for (int off = 16; off >= npad; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < npad) sred[warp][lane] = val;
+  __syncthreads();
+  if (threadIdx.x < npad) {
+    double s = 0.0;
+    int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) s += sred[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * DL_MAXC + threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Error plumbing: every launcher returns cudaError_t; the API layer maps it.
+#define DL_CUDA_TRY(expr)                       \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return _e;           \
+  } while (0)
+
+// Epilogue parameters of a hop kernel for one lattice:
+//   out = T1 (c * D^{(dag)} in + T2 aux),  T = a + i b gamma_5
+struct Epi {
+  double c, a1, b1, a2, b2;
+};
+struct EpiSet {
+  Epi e[DL_MAX_LAT];
+};
+
+enum { EPI_PLAIN = 0, EPI_AUX = 1, EPI_AUX_NORM = 2, EPI_CG = 3 };
+
+struct GaugeSet {
+  const void* g64;
+  const void* g32;
+  const void* g16;
+};
+
+// Every kernel launch is counted (host side) for the launch statistics of the C ABI.
+void dl_count_launch();
+#define DL_COUNT() dl_count_launch()
+
+// Launchers (defined in the .cu files).
+namespace dl {
+int blocks_for(Batch& B, int threads);  // fills blk_begin, returns the grid size
+cudaError_t dslash(const Batch& Bin, int prec, int grec, int epi, bool dag, int out_parity, FieldRef in, FieldRef aux,
+                   FieldRef out, const GaugeSet& g, const EpiSet& ep, const int* active, double* partial,
+                   FieldRef cg_r, FieldRef cg_y, FieldRef cg_p, const double* alpha, cudaStream_t st);
+}  // namespace dl

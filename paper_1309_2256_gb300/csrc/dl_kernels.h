@@ -1,0 +1,61 @@
+// Launchers shared between the discloop translation units (host side).
+#pragma once
+
+#include "dl_internal.cuh"
+
+// Per-column CG scalars, struct of arrays: S[slot * DL_NCMAX + gc]
+#define DL_NCMAX 256
+#define DL_NS 8
+#define DL_S_RR 0
+#define DL_S_RR0 1
+#define DL_S_ALPHA 2
+#define DL_S_BETA 3
+#define DL_S_PAP 4
+#define DL_S_MAXR 5
+#define DL_S_RRNEW 6
+#define DL_S_TMP 7
+
+#define DL_FLAG_CONVERGED 1
+#define DL_FLAG_BREAKDOWN 2
+#define DL_FLAG_UPDATE 4
+
+namespace dl {
+// blas
+cudaError_t copy(const Batch& B, int pd, int ps, FieldRef dst, FieldRef src, const int* mask, cudaStream_t st);
+cudaError_t accum(const Batch& B, int ph, int pl, FieldRef x, FieldRef y, const int* mask, int zero_y, cudaStream_t st);
+cudaError_t xmy_norm(const Batch& B, int prec, FieldRef r, FieldRef b, FieldRef a, const int* mask, double* partial,
+                     cudaStream_t st);
+cudaError_t norm2(const Batch& B, int prec, FieldRef v, const int* mask, double* partial, cudaStream_t st);
+cudaError_t xpay(const Batch& B, int prec, FieldRef p, FieldRef r, const double* beta, const int* mask, cudaStream_t st);
+cudaError_t twist(const Batch& B, int prec, FieldRef out, FieldRef in, const EpiSet& ep, const int* mask, cudaStream_t st);
+cudaError_t zero(const Batch& B, int prec, FieldRef v, const int* mask, cudaStream_t st);
+cudaError_t sum_partials(const Batch& B, const double* partial, double* out, int stride, int slot, int ncols_total,
+                         cudaStream_t st);
+cudaError_t cg_alpha(int ncols, double* S, int* active, int* flags, cudaStream_t st);
+cudaError_t cg_beta(int ncols, double* S, int* active, int* flags, int* iters, double tol2, double delta, cudaStream_t st);
+
+// layout (single-lattice batches)
+cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void* natural, int dtype, cudaStream_t st);
+cudaError_t unpack(const Batch& B, int prec, int parity, void* natural, FieldRef src, int dtype, cudaStream_t st);
+cudaError_t noise_z4(const Batch& B, int prec, int parity, FieldRef dst, unsigned long long seed,
+                     unsigned long long first, int quadrant, cudaStream_t st);
+cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* g32, int rec32, void* g16, int rec16,
+                       cudaStream_t st);
+
+// contractions
+cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+                           FieldRef eta_o, const void* g64, double2* W, cudaStream_t st);
+cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
+                     cudaStream_t st);
+cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
+                              const double2* G3, double pre_re, double pre_im, double2* out, int accumulate,
+                              cudaStream_t st);
+cudaError_t hpe_exact(double kappa, double amu, int flavour, double2* out16, cudaStream_t st);
+cudaError_t add_exact_p0(const Batch& B, int np, int nd, int ip0, const double2* exact16, double scale, double2* out,
+                         cudaStream_t st);
+cudaError_t col_accumulate(const double2* blk, const double2* sub, int ncol, long long per_col, double sign, double2* acc,
+                           cudaStream_t st);
+cudaError_t observables(const double2* l1, const double2* l2, int ncol, int T, int np, int nd, int ip0, double* obs,
+                        cudaStream_t st);
+cudaError_t combine(const double2* x, const double2* y, double a, double b, long long n, double2* out, cudaStream_t st);
+}  // namespace dl

@@ -1,0 +1,238 @@
+// Layout kernels: natural <-> even-odd device fields, gauge compression
+// (reconstruct 18/12/8, App. A "Twisted mass fermion operator"), and the
+// counter-based Z4 noise of the stochastic estimator (Sec. 2.1).
+#include "dl_internal.cuh"
+#include "dl_kernels.h"
+
+namespace {
+
+// Natural field (one lattice): complex [col][lex][12], dtype C128 (0) or C64 (1).
+template <int P>
+__global__ void pack_kernel(Batch B, int parity, FieldRef dst, const void* natural, int dtype) {
+  const LatDesc& L = B.lat[0];
+  const int npad = 1 << L.lognpad;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nitems = (long long)L.Vh * npad;
+  if (j >= nitems) return;
+  const int col = (int)(j & (npad - 1));
+  const int i = (int)(j >> L.lognpad);
+  typename SIO<P>::real v[24];
+  if (col < L.ncol) {
+    int x, y, z, t;
+    cb_coords(L, i, parity, x, y, z, t);
+    const long long V = 2LL * L.Vh;
+    const long long base = ((long long)col * V + lex_of(L, x, y, z, t)) * 12;
+    if (dtype == 0) {
+      const double2* src = (const double2*)natural + base;
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        double2 c = src[m];
+        v[2 * m] = (typename SIO<P>::real)c.x;
+        v[2 * m + 1] = (typename SIO<P>::real)c.y;
+      }
+    } else {
+      const float2* src = (const float2*)natural + base;
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        float2 c = src[m];
+        v[2 * m] = (typename SIO<P>::real)c.x;
+        v[2 * m + 1] = (typename SIO<P>::real)c.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 24; ++m) v[m] = 0;
+  }
+  SIO<P>::store(seg_ptr_w<P>(dst, L), seg_norm(dst, L), nitems, j, v);
+}
+
+template <int P>
+__global__ void unpack_kernel(Batch B, int parity, void* natural, FieldRef src, int dtype) {
+  const LatDesc& L = B.lat[0];
+  const int npad = 1 << L.lognpad;
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nitems = (long long)L.Vh * npad;
+  if (j >= nitems) return;
+  const int col = (int)(j & (npad - 1));
+  if (col >= L.ncol) return;
+  const int i = (int)(j >> L.lognpad);
+  int x, y, z, t;
+  cb_coords(L, i, parity, x, y, z, t);
+  typename SIO<P>::real v[24];
+  SIO<P>::load(seg_ptr<P>(src, L), seg_norm(src, L), nitems, j, v);
+  const long long V = 2LL * L.Vh;
+  const long long base = ((long long)col * V + lex_of(L, x, y, z, t)) * 12;
+  if (dtype == 0) {
+    double2* d = (double2*)natural + base;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) d[m] = make_double2((double)v[2 * m], (double)v[2 * m + 1]);
+  } else {
+    float2* d = (float2*)natural + base;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) d[m] = make_float2((float)v[2 * m], (float)v[2 * m + 1]);
+  }
+}
+
+// splitmix64 (Steele, Lea & Flood 2014): state = seed + (n + 1) * golden, then
+// the published output mix.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed, unsigned long long n) {
+  unsigned long long z = seed + (n + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Entry (noise r, lex, spin a, colour c) from bits 0 and 1 of
+// splitmix64(seed, (r*V + lex)*12 + 3a + c): (s1 + i s2)/sqrt(2) with
+// s = 1 - 2*bit, or {1, i, -1, -i}[bit0 + 2*bit1] for the quadrant form.
+template <int P>
+__global__ void noise_kernel(Batch B, int parity, FieldRef dst, unsigned long long seed, unsigned long long first,
+                             int quadrant) {
+  const int l = find_lat(B, blockIdx.x);
+  const LatDesc& L = B.lat[l];
+  const int npad = 1 << L.lognpad;
+  const long long j = (long long)(blockIdx.x - B.blk_begin[l]) * blockDim.x + threadIdx.x;
+  const long long nitems = (long long)L.Vh * npad;
+  if (j >= nitems) return;
+  const int col = (int)(j & (npad - 1));
+  const int i = (int)(j >> L.lognpad);
+  typename SIO<P>::real v[24];
+  if (col < L.ncol) {
+    int x, y, z, t;
+    cb_coords(L, i, parity, x, y, z, t);
+    const unsigned long long V = 2ULL * (unsigned long long)L.Vh;
+    const unsigned long long r = first + (unsigned long long)col;
+    const unsigned long long n0 = (r * V + (unsigned long long)lex_of(L, x, y, z, t)) * 12ULL;
+    const double h = 1.0 / sqrt(2.0);
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      unsigned long long w = splitmix64(seed, n0 + (unsigned long long)m);
+      int b0 = (int)(w & 1ULL), b1 = (int)((w >> 1) & 1ULL);
+      double re, im;
+      if (quadrant) {
+        int qd = b0 + 2 * b1;
+        re = (qd == 0) ? 1.0 : (qd == 2 ? -1.0 : 0.0);
+        im = (qd == 1) ? 1.0 : (qd == 3 ? -1.0 : 0.0);
+      } else {
+        re = (1.0 - 2.0 * b0) * h;
+        im = (1.0 - 2.0 * b1) * h;
+      }
+      v[2 * m] = (typename SIO<P>::real)re;
+      v[2 * m + 1] = (typename SIO<P>::real)im;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 24; ++m) v[m] = 0;
+  }
+  SIO<P>::store(seg_ptr_w<P>(dst, L), seg_norm(dst, L), nitems, j, v);
+}
+
+// Gauge compression: thread per lexicographic site, all four directions.
+__global__ void pack_gauge_kernel(LatDesc L, const double2* __restrict__ links, double2* g64, void* g32, int rec32,
+                                  void* g16, int rec16) {
+  const int lex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int V = 2 * L.Vh;
+  if (lex >= V) return;
+  int x = lex % L.X, r = lex / L.X;
+  int y = r % L.Y;
+  r /= L.Y;
+  int z = r % L.Z, t = r / L.Z;
+  const int p = (x + y + z + t) & 1;
+  const int i = lex >> 1;
+  const int Vh = L.Vh;
+  for (int mu = 0; mu < 4; ++mu) {
+    const double2* u = links + ((size_t)lex * 4 + mu) * 9;
+    double2 e[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) e[k] = u[k];
+    const size_t blk = (size_t)(p * 4 + mu);
+    if (g64) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) g64[(blk * 9 + k) * Vh + i] = e[k];
+    }
+    if (g32) {
+      float4* g = (float4*)g32;
+      if (rec32 == 12) {
+        g[(blk * 3 + 0) * Vh + i] = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+        g[(blk * 3 + 1) * Vh + i] = make_float4(e[2].x, e[2].y, e[3].x, e[3].y);
+        g[(blk * 3 + 2) * Vh + i] = make_float4(e[4].x, e[4].y, e[5].x, e[5].y);
+      } else {
+        float ta = (float)atan2(e[0].y, e[0].x), tc = (float)atan2(e[6].y, e[6].x);
+        g[(blk * 2 + 0) * Vh + i] = make_float4(e[1].x, e[1].y, e[2].x, e[2].y);
+        g[(blk * 2 + 1) * Vh + i] = make_float4(e[3].x, e[3].y, ta, tc);
+      }
+    }
+    if (g16) {
+      if (rec16 == 12) {
+        uint2* g = (uint2*)g16;
+        for (int k = 0; k < 3; ++k) {
+          uint2 c;
+          __half2* h = reinterpret_cast<__half2*>(&c);
+          h[0] = __floats2half2_rn((float)e[2 * k].x, (float)e[2 * k].y);
+          h[1] = __floats2half2_rn((float)e[2 * k + 1].x, (float)e[2 * k + 1].y);
+          g[(blk * 3 + k) * Vh + i] = c;
+        }
+      } else {
+        uint4* g = (uint4*)g16;
+        const double ipi = 1.0 / 3.14159265358979323846;
+        uint4 c;
+        __half2* h = reinterpret_cast<__half2*>(&c);
+        h[0] = __floats2half2_rn((float)e[1].x, (float)e[1].y);
+        h[1] = __floats2half2_rn((float)e[2].x, (float)e[2].y);
+        h[2] = __floats2half2_rn((float)e[3].x, (float)e[3].y);
+        h[3] = __floats2half2_rn((float)(atan2(e[0].y, e[0].x) * ipi), (float)(atan2(e[6].y, e[6].x) * ipi));
+        g[blk * Vh + i] = c;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+namespace dl {
+
+#define DISPATCH_P(prec, CALL) \
+  switch (prec) {              \
+    case P64: { constexpr int PP = P64; CALL; } break; \
+    case P32: { constexpr int PP = P32; CALL; } break; \
+    case P16: { constexpr int PP = P16; CALL; } break; \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void* natural, int dtype, cudaStream_t st) {
+  long long items = (long long)B.lat[0].Vh << B.lat[0].lognpad;
+  int g = (int)((items + 255) / 256);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (pack_kernel<PP><<<g, 256, 0, st>>>(B, parity, dst, natural, dtype)));
+  return cudaGetLastError();
+}
+
+cudaError_t unpack(const Batch& B, int prec, int parity, void* natural, FieldRef src, int dtype, cudaStream_t st) {
+  long long items = (long long)B.lat[0].Vh << B.lat[0].lognpad;
+  int g = (int)((items + 255) / 256);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (unpack_kernel<PP><<<g, 256, 0, st>>>(B, parity, natural, src, dtype)));
+  return cudaGetLastError();
+}
+
+cudaError_t noise_z4(const Batch& Bin, int prec, int parity, FieldRef dst, unsigned long long seed,
+                     unsigned long long first, int quadrant, cudaStream_t st) {
+  Batch B = Bin;
+  int g = blocks_for(B, 256);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  DISPATCH_P(prec, (noise_kernel<PP><<<g, 256, 0, st>>>(B, parity, dst, seed, first, quadrant)));
+  return cudaGetLastError();
+}
+
+cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* g32, int rec32, void* g16, int rec16,
+                       cudaStream_t st) {
+  int V = 2 * L.Vh;
+  DL_COUNT();
+  pack_gauge_kernel<<<(V + 127) / 128, 128, 0, st>>>(L, (const double2*)links_dev, (double2*)g64, g32, rec32, g16, rec16);
+  return cudaGetLastError();
+}
+
+}  // namespace dl
