@@ -9,9 +9,9 @@ operator, batched 16 right-hand sides per launch, each solution contracted
 into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
 (4 exact orders) local loops for all 16 Gamma, every t, |p|^2 <= 9.
 
-One step = one quarter of the TSM sweep (6 HP-LP pairs + 125 fresh LP solves
-with their contractions; 4 steps = the full N_HP = 24, N_LP = 500 sweep) on
-noise vectors the step has not used before.
+One step = one full TSM sweep for the gauge field (24 HP-LP pairs + 500 fresh
+LP solves with their contractions: the paper's unit of work per configuration)
+on noise vectors no other step has used.
 
 value = loop estimates per second at equal statistical error: the number of
 plain high-precision loop estimates (one per noise vector) that would give the
@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 DIMS = (32, 32, 32, 64)
 EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
-N_HP, N_LP, SLICES, BLOCK = 24, 500, 4, 16
+N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 16
 TOL_HP, TOL_LP = 1e-10, 1e-2
 P2MAX = 9
 LINK_SEED, NOISE_SEED = 1002, 2002
@@ -123,6 +123,22 @@ def _equal_error(obs_hp, obs_pair, obs_lp, n_hp, n_lp, t_step):
     return out
 
 
+def rank_seed(step: int, rank: int) -> int:
+    """Noise seed of a sweep: distinct for every (step, rank), so replicas never share noise."""
+    return NOISE_SEED + 1000003 * (step + 1) + 7919 * rank
+
+
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's timed region (the job finishes when every replica has)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _links():
     import synth
     return synth.gauge_links(DIMS, EPS, LINK_SEED)
@@ -138,14 +154,14 @@ def run_ours(args, rank, world, device):
     n_hp_s, n_lp_s = N_HP // SLICES, N_LP // SLICES
     stream = torch.cuda.current_stream()
     ctx = dl.dl_create(DIMS, device, stream)
-    dl.dl_load_gauge(ctx, links, -1.0, 12, 8)
+    dl.dl_load_gauge(ctx, links, -1.0, 12, 12)
     dl.dl_set_params(ctx, KAPPA, AMU)
     npm = len(dl.dl_momenta(P2MAX))
 
     def params(step):
         return dl.dl_tsm_params(n_hp=n_hp_s, n_lp=n_lp_s, tol_hp=TOL_HP, tol_lp=TOL_LP, prec_hp_lo=dl.DL_F32,
                                 prec_lp_lo=dl.DL_F16, delta_hp=0.1, block=BLOCK,
-                                seed=NOISE_SEED + 1000003 * (step + 1) + 7919 * rank, p2max=P2MAX, with_deriv=0,
+                                seed=rank_seed(step, rank), p2max=P2MAX, with_deriv=0,
                                 hpe=1, max_iter=200000, chunk=32)
 
     loops = np.zeros((3, DIMS[3], npm, 1, 4, 4), dtype=np.complex128)
@@ -185,10 +201,7 @@ def run_ours(args, rank, world, device):
     launches = dl.dl_kernel_launches() - launches0
     prof = dl.dl_profile(ctx, 0)
     ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     t_step = ms / 1e3 / args.steps
 
     # e2e: the same step through the C ABI from pinned host memory (gauge field
@@ -198,7 +211,7 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        dl.lib().dl_load_gauge(ctx, pinned.data_ptr(), 0, -1.0, 12, 8)
+        dl.lib().dl_load_gauge(ctx, pinned.data_ptr(), 0, -1.0, 12, 12)
         step(1000 + i, False)
     torch.cuda.synchronize()
     e2e_t = (time.perf_counter() - t0) / e2e_steps
@@ -213,7 +226,7 @@ def run_ours(args, rank, world, device):
     eq = _equal_error(ohp, opr, olp, n_hp_s, n_lp_s, t_step)
     value = min(eq["sigma"]["per_s"], eq["axial"]["per_s"]) * world
     e2e_value = min(eq["sigma"]["plain_equiv_per_step"], eq["axial"]["plain_equiv_per_step"]) / e2e_t * world
-    roof = roofline(prof, t_step)
+    roof = roofline(prof, infos)
     it_hp = sum(i.iters_hp for i in infos) / max(1, len(infos) * n_hp_s)
     it_lp = sum(i.iters_lp for i in infos) / max(1, len(infos) * (n_hp_s + n_lp_s))
     return dict(value=value, t_step=t_step, wall=wall, eq=eq, roof=roof, launches=launches, ref=ref, e2e=e2e_value,
@@ -246,14 +259,20 @@ def plain_fp64_reference(dl, ctx, device, infos, n_hp_s):
             "how": f"{n_it} CG iterations timed, scaled by the mean HP iteration count"}
 
 
-def roofline(prof, t_step):
-    """Dominant stencil launch: algorithmic bytes per launch / average duration."""
+def roofline(prof, infos):
+    """Dominant stencil kernel: algorithmic bytes per launch / average launch duration.
+
+    Durations come from CUDA events recorded inside the solver's graphs around the
+    four stencil launches of the first iteration of every chunk (dl_profile).  The
+    dominant (stage, precision) is the one with the largest average duration times
+    its number of block-iterations in the sweep."""
     peaks, kind = _peaks()
     V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
     Vh = V // 2
-    link_b = {0: 144, 1: 48, 2: 16}  # FP64 recon 18, FP32 recon 12, FP16 recon 8
-    sp_b = {0: 192, 1: 96, 2: 52}    # spinor bytes per site (FP16: 48 + 4-byte norm)
+    link_b = {0: 144, 1: 48, 2: 24}  # FP64 recon 18, FP32 recon 12, 16-bit recon 12 (as loaded)
+    sp_b = {0: 192, 1: 96, 2: 52}    # spinor bytes per site (16-bit: 48 + 4-byte scale)
     units = {0: 2, 1: 3, 2: 2, 3: 7}  # spinor streams per stage (in, aux, out, r, y, p ...)
+    col_its = {1: sum(i.iters_hp for i in infos), 2: sum(i.iters_lp for i in infos)}
     best = None
     for stage in range(4):
         for prec in range(3):
@@ -263,10 +282,11 @@ def roofline(prof, t_step):
             cols = items / n / Vh
             bytes_launch = 4 * V * link_b[prec] + units[stage] * Vh * cols * sp_b[prec]
             avg = ms / n / 1e3
-            rec = {"stage": stage, "prec": ["f64", "f32", "f16"][prec], "launches_sampled": int(n),
+            weight = avg * col_its.get(prec, 0) / max(cols, 1e-9)
+            rec = {"stage": stage, "prec": ["f64", "f32", "16-bit"][prec], "launches_sampled": int(n),
                    "avg_ms": avg * 1e3, "cols": cols, "bytes": bytes_launch, "gbs": bytes_launch / avg / 1e9,
-                   "total_ms": ms}
-            if best is None or ms > best["total_ms"]:
+                   "weight": weight}
+            if best is None or weight > best["weight"]:
                 best = rec
     if best is None:
         return None
@@ -274,7 +294,8 @@ def roofline(prof, t_step):
     return {"bound": "hbm", "achieved": round(best["gbs"], 1), "peak": peak, "unit": "GB/s",
             "frac": round(best["gbs"] / peak, 4), "traffic": None,
             "kernel": f"dslash stage {best['stage']} ({best['prec']} Krylov, {best['cols']:.1f} columns)",
-            "bytes_per_launch": best["bytes"], "avg_launch_ms": round(best["avg_ms"], 4), "peak_kind": kind}
+            "bytes_per_launch": int(best["bytes"]), "avg_launch_ms": round(best["avg_ms"], 4),
+            "peak_kind": kind + " (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else kind}
 
 
 def cpu_oracle_sample():
@@ -293,13 +314,48 @@ def cpu_oracle_sample():
     return dt, 1
 
 
+def stencil_case():
+    """Small case for ncu captures: 24^3 x 24, 16 right-hand sides, one 16-bit and one
+    FP32 Krylov solve of 4 CG iterations each (fields 138 MB / 255 MB, above the
+    129 MB L2; about 5 GB on the device)."""
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+    import synth
+    dims = (24, 24, 24, 24)
+    links = synth.gauge_links(dims, EPS, 77)
+    ctx = dl.dl_create(dims, 0, torch.cuda.current_stream())
+    dl.dl_load_gauge(ctx, links, -1.0, 12, 12)
+    dl.dl_set_params(ctx, KAPPA, AMU)
+    n = 16
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    eta = torch.empty((n, V * 12), dtype=torch.complex64, device="cuda")
+    dl.dl_noise_z4(ctx, 9, 0, n, eta, dl.DL_C64)
+    sol = torch.empty_like(eta)
+    dl.dl_profile(ctx, 1)
+    for lo in (dl.DL_F16, dl.DL_F32):
+        prm = dl.dl_solve_params(tol=1e-12, max_iter=4, prec_hi=dl.DL_F32, prec_lo=lo, delta=0.0, flavour=1, chunk=4)
+        st, stats = dl.dl_solve(ctx, eta, sol, n, dl.DL_C64, prm)
+    torch.cuda.synchronize()
+    prof = dl.dl_profile(ctx, 0)
+    dl.dl_destroy(ctx)
+    for prec, name in ((2, "16-bit"), (1, "f32")):
+        print(name, "stage ms:", " ".join(f"{prof[k, prec, 1] / max(prof[k, prec, 0], 1):.3f}" for k in range(4)))
+    print("stencil case done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default=None, choices=["stencil"],
+                    help="small profiling case instead of the benchmark (for ncu)")
     args = ap.parse_args()
+    if args.case == "stencil":
+        stencil_case()
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -341,7 +397,7 @@ def main():
         "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
                    "tol_hp": TOL_HP, "tol_lp": TOL_LP, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
-                   "step": "1/4 of the TSM sweep: 6 HP-LP pairs + 125 LP solves + contractions",
+                   "step": "one TSM sweep: 24 HP-LP pairs + 500 LP solves + contractions",
                    "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": ro,
@@ -361,23 +417,38 @@ def main():
     print(json.dumps(line))
 
 
+# CG iterations of one high-precision (1e-10) solve on this workload, measured by
+# the GPU path (FP32 Krylov + FP64 reliable updates, mean over noise vectors); the
+# plain FP64 method needs the same Krylov iterations in exact arithmetic.
+HP_ITERS_MEASURED = 71.0
+
+
 def run_reference(args, world):
-    """The oracle as it stands on the host cores, same metric and config: each step
-    is a bounded sample (one oracle CG iteration at full size) scaled to a step."""
+    """The oracle as it stands on the host cores, same metric, config and unit.
+    The oracle is the plain method (FP64 CG on every noise vector, no TSM), so each
+    of its loop estimates counts one at equal error.  A step is a bounded sample:
+    one oracle CG iteration on the full 32^3 x 64 lattice, scaled by the HP
+    iteration count of the workload."""
     per = []
     for _ in range(args.warmup):
         cpu_oracle_sample()
+    cores = 1
     for _ in range(args.steps):
-        per.append(cpu_oracle_sample()[0])
+        dt, cores = cpu_oracle_sample()
+        per.append(dt)
     t_it = float(np.median(per))
-    line = {"impl": "reference", "metric": "loop estimates/sec at 32^3x64 at equal error (TSM vs plain HP estimates); "
-                                           "Dslash HBM GB/s",
-            "value": None, "unit": "loop estimates/s (equal error)", "n_gpus": world, "steps": args.steps,
+    value = 1.0 / (t_it * HP_ITERS_MEASURED)
+    line = {"impl": "reference",
+            "metric": "loop estimates/sec at 32^3x64 at equal error (TSM vs plain HP estimates); Dslash HBM GB/s",
+            "value": value, "unit": "loop estimates/s (equal error)", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_it * 1e3, 1), "higher_is_better": True,
-            "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": None,
-                             "sample": "one FP64 oracle CG iteration on 32^3x64 per step"},
-            "e2e": {"value": None, "unit": "loop estimates/s (equal error)", "h2d_bytes_per_step": 0,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU,
+                       "method": "plain FP64 CG per noise vector (the oracle)", "hp_iters": HP_ITERS_MEASURED},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
+                             "sample": f"one FP64 oracle CG iteration on 32^3x64 per step ({t_it:.1f} s), "
+                                       f"x {HP_ITERS_MEASURED:.0f} iterations per HP estimate; contractions excluded"},
+            "e2e": {"value": value, "unit": "loop estimates/s (equal error)", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

@@ -54,7 +54,11 @@ typedef enum {
   DL_BREAKDOWN = 3      /* a CG scalar became zero, negative or non-finite */
 } dl_status;
 
-typedef enum { DL_F64 = 0, DL_F32 = 1, DL_F16 = 2 } dl_prec;     /* storage precision */
+/* Storage precision.  DL_F16 is the 16-bit format: signed 16-bit fixed point
+ * with one float scale per site and right-hand side (value = q * scale / 32767,
+ * scale = the site's largest |re|,|im|), i.e. the paper's "half" precision
+ * (App. A, Table A.1); arithmetic on it is FP32. */
+typedef enum { DL_F64 = 0, DL_F32 = 1, DL_F16 = 2 } dl_prec;
 typedef enum { DL_C128 = 0, DL_C64 = 1 } dl_dtype;              /* natural field element type */
 
 /* Operators applied by dl_apply (natural full-lattice fields in and out). */
@@ -90,7 +94,7 @@ const char* dl_last_error(const dl_ctx* ctx);
 dl_status dl_set_stream(dl_ctx* ctx, void* cuda_stream);
 
 /* Load the gauge field (App. A, "Twisted mass fermion operator": links stored
- * with 18, 12 or 8 reals).  `links` is complex128 [T][Z][Y][X][4][3][3] in host
+ * with 18, 12 or 8 reals; the 16-bit copy uses int16 fixed point).  `links` is complex128 [T][Z][Y][X][4][3][3] in host
  * memory (links_on_device = 0) or device memory (1).  t_boundary = -1
  * (antiperiodic in time, the default reading) or +1.  recon_f32 in {18,12,8}
  * and recon_f16 in {12,8} choose the compressed copies the FP32 and FP16

@@ -14,6 +14,8 @@ LIB = os.path.join(HERE, "libdiscloop.so")
 SOURCES = ["dl_dslash.cu", "dl_blas.cu", "dl_layout.cu", "dl_contract.cu", "dl_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# extra nvcc flags, e.g. DL_NVCC_EXTRA="-DDL_MINB=3" to build a variant of the stencil
+FLAGS += os.environ.get("DL_NVCC_EXTRA", "").split()
 
 
 def _nvcc():

@@ -64,6 +64,8 @@ struct dl_ctx {
   std::map<std::string, Field> ws;
   double* partial = nullptr;
   size_t partial_blocks = 0;
+  int* loopctr = nullptr;  // iterations run by the current graph launch, and its limit
+  int* waitc = nullptr;    // per column: iterations spent waiting for a reliable update
   double* S = nullptr;  // [DL_NS][DL_NCMAX]
   int* active = nullptr;
   int* flags = nullptr;
@@ -80,6 +82,7 @@ struct dl_ctx {
   // live stencil timing: events around the four operator launches of the first
   // CG iteration of every captured chunk; sums per (stage, precision)
   int profiling = 0;
+  int prof_pending[3] = {0, 0, 0};  // take one stencil sample per precision when set
   cudaEvent_t pev[8] = {nullptr};
   double prof_ms[4][3] = {{0}};
   long long prof_n[4][3] = {{0}};
@@ -123,6 +126,7 @@ Batch make_batch(const dl_ctx* c, int ncol) {
   L.tbc = c->tbc;
   L.kappa = c->kappa;
   L.amu = c->amu;
+  B.pstride = (int)c->partial_blocks;
   dl::blocks_for(B, 256);
   return B;
 }
@@ -186,15 +190,12 @@ dl_status ensure_field(dl_ctx* c, const std::string& base, int prec, int ncol, F
   return DL_OK;
 }
 
+// The partial-sum buffer holds DL_MAXC columns of pstride blocks, enough for any
+// launch on this context (256-thread blocks over Vh * 32 items); allocated once.
 dl_status ensure_partial(dl_ctx* c, const Batch& B) {
   size_t nb = (size_t)B.blk_begin[B.nlat];
   if (nb <= c->partial_blocks) return DL_OK;
-  if (c->partial) cudaFree(c->partial);
-  c->partial = nullptr;
-  CK(cudaMalloc((void**)&c->partial, std::max<size_t>(nb, 1) * DL_MAXC * sizeof(double)));
-  c->partial_blocks = nb;
-  invalidate_graphs(c);
-  return DL_OK;
+  return fail(c, DL_ERR_STATE, "partial-sum buffer smaller than a launch");
 }
 
 dl_status ensure_scratch(dl_ctx* c, size_t bytes) {
@@ -306,32 +307,54 @@ struct CGFields {
 };
 
 // One CG iteration for all active columns (low precision); graph-capturable.
-cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta,
-                         bool timed = false) {
+cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta) {
   const int n = B.lat[0].ncol;
-  auto ev = [&](int k) { return timed ? cudaEventRecord(c->pev[k], c->st) : cudaSuccess; };
-  DL_CUDA_TRY(ev(0));
   DL_CUDA_TRY(stage1(c, B, lo, false, f, F.p->ref(), F.t1->ref(), c->active));
-  DL_CUDA_TRY(ev(1));
-  DL_CUDA_TRY(ev(2));
   DL_CUDA_TRY(stage2(c, B, lo, false, f, F.t1->ref(), F.p->ref(), F.q->ref(), c->active, c->partial));
-  DL_CUDA_TRY(ev(3));
   DL_CUDA_TRY(colsum(c, B, DL_S_PAP));
   DL_CUDA_TRY(dl::cg_alpha(n, c->S, c->active, c->flags, c->st));
-  DL_CUDA_TRY(ev(4));
   DL_CUDA_TRY(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), c->active));
-  DL_CUDA_TRY(ev(5));
   {
     EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, -f);
     GaugeSet g{c->g64, c->g32, c->g16};
-    DL_CUDA_TRY(ev(6));
     DL_CUDA_TRY(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, c->active,
                            c->partial, F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
-    DL_CUDA_TRY(ev(7));
   }
   DL_CUDA_TRY(colsum(c, B, DL_S_RRNEW));
   DL_CUDA_TRY(dl::cg_beta(n, c->S, c->active, c->flags, c->iters, tol2, delta, c->st));
   return dl::xpay(B, lo, F.p->ref(), F.r->ref(), c->S + DL_S_BETA * DL_NCMAX, c->active, c->st);
+}
+
+// One timed application of the four stencil stages of an iteration (all columns,
+// outside the solver's graph) on the solver's current fields; used by dl_profile.
+// Runs after a solve has finished: it leaves r and y modified, which the next
+// solve re-initialises.
+dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F) {
+  GaugeSet g{c->g64, c->g32, c->g16};
+  cudaEvent_t* ev = c->pev;
+  CK(cudaEventRecord(ev[0], c->st));
+  CK(stage1(c, B, lo, false, f, F.p->ref(), F.t1->ref(), nullptr));
+  CK(cudaEventRecord(ev[1], c->st));
+  CK(cudaEventRecord(ev[2], c->st));
+  CK(stage2(c, B, lo, false, f, F.t1->ref(), F.p->ref(), F.q->ref(), nullptr, c->partial));
+  CK(cudaEventRecord(ev[3], c->st));
+  CK(cudaEventRecord(ev[4], c->st));
+  CK(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), nullptr));
+  CK(cudaEventRecord(ev[5], c->st));
+  EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, -f);
+  CK(cudaEventRecord(ev[6], c->st));
+  CK(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, nullptr, c->partial,
+                F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
+  CK(cudaEventRecord(ev[7], c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int k = 0; k < 4; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    c->prof_ms[k][lo] += ms;
+    c->prof_n[k][lo] += 1;
+    c->prof_items[k][lo] += (long long)c->Vh * B.lat[0].ncol;
+  }
+  return DL_OK;
 }
 
 // Reliable update for the columns in `mask` (host vector): x += y, y = 0,
@@ -353,42 +376,60 @@ dl_status reliable_update(dl_ctx* c, const Batch& B, int hi, int lo, int f, cons
   return DL_OK;
 }
 
-std::string graph_key(const dl_ctx* c, int lo, int f, int n, int chunk, double tol2, double delta, const CGFields& F) {
+std::string graph_key(const dl_ctx* c, int lo, int f, int n, double tol2, double delta, const CGFields& F) {
   char buf[512];
-  snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%p|%p|%p|%p|%p|%p|%p|%d|%d|%d", lo, f, n, chunk, tol2,
-           delta, c->kappa, c->amu, F.r->data, F.p->data, F.y->data, F.t1->data, F.q->data, F.t2->data,
-           (void*)c->partial, c->rec32, c->rec16, c->profiling);
+  snprintf(buf, sizeof(buf), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%p|%p|%p|%p|%p|%p|%p|%d|%d", lo, f, n, tol2, delta,
+           c->kappa, c->amu, F.r->data, F.p->data, F.y->data, F.t1->data, F.q->data, F.t2->data, (void*)c->partial,
+           c->rec32, c->rec16);
   return std::string(buf);
 }
 
-dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, int chunk, double tol2, double delta,
-                    cudaGraphExec_t* out) {
-  std::string key = graph_key(c, lo, f, B.lat[0].ncol, chunk, tol2, delta, F);
+// The solver's graph: a conditional WHILE node whose body is one CG iteration
+// followed by cg_cond, which stops the loop on the device as soon as no column
+// is active, a column waits for a reliable update, or the launch's iteration
+// limit (loopctr[1]) is reached.  One launch runs as many iterations as needed.
+dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta,
+                    GraphEntry** out) {
+  std::string key = graph_key(c, lo, f, B.lat[0].ncol, tol2, delta, F);
   for (auto& g : c->graphs)
     if (g.key == key) {
-      *out = g.exec;
+      *out = &g;
       return DL_OK;
     }
-  if (c->profiling && c->graphs.size() >= 4) invalidate_graphs(c);
-  cudaGraph_t graph;
+  cudaGraph_t outer;
+  CK(cudaGraphCreate(&outer, 0));
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, outer, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
   const long long before = g_launches.load();
-  CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = cg_iteration(c, B, lo, f, F, tol2, delta, c->profiling && k == 0);
-  cudaError_t e2 = cudaStreamEndCapture(c->st, &graph);
-  if (e != cudaSuccess) return cuda_fail(c, e, "capture of the CG iteration");
+  CK(cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cg_iteration(c, B, lo, f, F, tol2, delta);
+  if (e == cudaSuccess) e = dl::cg_cond(B.lat[0].ncol, c->active, c->flags, c->loopctr, c->loopctr + 1, c->waitc, h, c->st);
+  cudaGraph_t captured;
+  cudaError_t e2 = cudaStreamEndCapture(c->st, &captured);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(outer);
+    return cuda_fail(c, e, "capture of the CG iteration");
+  }
   CK(e2);
   cudaGraphExec_t exec;
-  CK(cudaGraphInstantiate(&exec, graph, 0));
-  cudaGraphDestroy(graph);
-  if (c->graphs.size() >= 4) {
+  CK(cudaGraphInstantiate(&exec, outer, 0));
+  cudaGraphDestroy(outer);
+  const long long nodes = g_launches.load() - before;
+  g_launches.fetch_sub(nodes);  // counted per executed iteration, not at capture
+  if (c->graphs.size() >= 8) {
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  const long long nodes = g_launches.load() - before;
-  g_launches.fetch_sub(nodes);  // counted when the graph runs, not when it is captured
   c->graphs.push_back(GraphEntry{key, exec, nodes});
-  *out = exec;
+  *out = &c->graphs.back();
   return DL_OK;
 }
 
@@ -424,14 +465,16 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
   }
   h.iters.assign(n, 0);
   CK(cudaMemcpyAsync(c->iters, h.iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
   if ((s = upload_state(c, n, h)) != DL_OK) return s;
   CK(dl::copy(B, lo, hi, F.r->ref(), b->ref(), nullptr, c->st));
   CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), nullptr, c->st));
   CK(dl::zero(B, lo, F.y->ref(), nullptr, c->st));
   const double tol2 = prm.tol * prm.tol;
-  const int chunk = std::max(1, prm.chunk);
-  cudaGraphExec_t gexec;
-  if ((s = get_graph(c, B, lo, f, F, chunk, tol2, prm.delta, &gexec)) != DL_OK) return s;
+  GraphEntry* ge;
+  if ((s = get_graph(c, B, lo, f, F, tol2, prm.delta, &ge)) != DL_OK) return s;
+  const cudaGraphExec_t gexec = ge->exec;
+  const long long body_kernels = ge->kernels;
   std::vector<int> finalized(n, 0), notconv(n, 0);
   for (int i = 0; i < n; ++i)
     if (!h.active[i]) finalized[i] = 1;  // zero right-hand side: x = 0
@@ -442,21 +485,16 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
     bool any = false;
     for (int i = 0; i < n; ++i) any |= (h.active[i] != 0);
     if (!any) break;
-    int n_act = 0;
-    for (int i = 0; i < n; ++i) n_act += h.active[i] != 0;
+    int itmin = prm.max_iter;
+    for (int i = 0; i < n; ++i)
+      if (h.active[i]) itmin = std::min(itmin, h.iters[i]);
+    const int ctr[2] = {0, std::max(1, std::min(prm.max_iter - itmin, 1 << 20))};
+    CK(cudaMemcpyAsync(c->loopctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, c->st));
     CK(cudaGraphLaunch(gexec, c->st));
-    for (auto& ge : c->graphs)
-      if (ge.exec == gexec) g_launches.fetch_add(ge.kernels);
+    int ran = 0;
+    CK(cudaMemcpyAsync(&ran, c->loopctr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     if ((s = download_state(c, n, h)) != DL_OK) return s;
-    if (c->profiling) {
-      for (int k = 0; k < 4; ++k) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->pev[2 * k], c->pev[2 * k + 1]));
-        c->prof_ms[k][lo] += ms;
-        c->prof_n[k][lo] += 1;
-        c->prof_items[k][lo] += (long long)c->Vh * n_act;
-      }
-    }
+    g_launches.fetch_add(body_kernels * ran);
     std::vector<int> mask(n, 0);
     bool need = false;
     for (int i = 0; i < n; ++i) {
@@ -496,6 +534,7 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
     if (!need) continue;
     std::vector<double> rr;
     if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) return s;
+    CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
     for (int i = 0; i < n; ++i) {
       if (!mask[i]) continue;
       ++n_rel;
@@ -552,6 +591,10 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
   }
   CK(cudaStreamSynchronize(c->st));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (c->profiling && c->prof_pending[lo]) {
+    c->prof_pending[lo] = 0;
+    if ((s = sample_stencil(c, B, lo, f, F)) != DL_OK) return s;
+  }
   int maxit = 0;
   bool anync = false;
   for (int i = 0; i < n; ++i) {
@@ -649,7 +692,8 @@ dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv
   const int npad = 1 << L.lognpad;
   const int ncomp = with_deriv ? 80 : 16;
   const size_t V = 2ull * L.Vh;
-  const size_t nW = (size_t)ncomp * V * npad;
+  const bool fused = L.X <= 256;  // one CTA per (row, column group) holds X * cw <= 256 sites
+  const size_t nW = fused ? 0 : (size_t)ncomp * V * npad;
   const size_t nG1 = (size_t)ncomp * L.T * L.Z * L.Y * NX * npad;
   const size_t nG2 = (size_t)ncomp * L.T * L.Z * NY * NX * npad;
   const size_t nG3 = (size_t)ncomp * L.T * NZ * NY * NX * npad;
@@ -661,11 +705,17 @@ dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv
   double2* G3 = G2 + nG2;
   double2* ph = G3 + nG3;
   if (L.X > (int)nph || L.Y > (int)nph || L.Z > (int)nph) return fail(c, DL_ERR_ARG, "spatial extent too large");
-  CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
-                        eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
-  CK(dl::dft_pass(W, G1, (long long)ncomp * L.T * L.Z * L.Y, L.X, npad, mx, ph, c->st));
-  CK(dl::dft_pass(G1, G2, (long long)ncomp * L.T * L.Z, L.Y, (long long)NX * npad, my, ph, c->st));
-  CK(dl::dft_pass(G2, G3, (long long)ncomp * L.T, L.Z, (long long)NY * NX * npad, mz, ph, c->st));
+  const int fp32 = prec != P64;
+  if (fused) {
+    CK(dl::contract_x(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
+                      eta_o ? eta_o->ref() : NOF, c->g64, mx, G1, c->st));
+  } else {
+    CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
+                          eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
+    CK(dl::dft_pass(W, G1, (long long)ncomp * L.T * L.Z * L.Y, L.X, npad, mx, ph, fp32, c->st));
+  }
+  CK(dl::dft_pass(G1, G2, (long long)ncomp * L.T * L.Z, L.Y, (long long)NX * npad, my, ph, fp32, c->st));
+  CK(dl::dft_pass(G2, G3, (long long)ncomp * L.T, L.Z, (long long)NY * NX * npad, mz, ph, fp32, c->st));
   CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, pre_re, pre_im, out, accumulate, c->st));
   return DL_OK;
 }
@@ -712,6 +762,7 @@ dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stre
   c->dev = device;
   memcpy(c->dims, dims, sizeof(int) * 4);
   c->Vh = (int)(V / 2);
+  c->partial_blocks = ((size_t)c->Vh * DL_MAXC + 255) / 256 + 8;
   c->user = (cudaStream_t)cuda_stream;
   cudaError_t e;
   if ((e = cudaSetDevice(device)) != cudaSuccess || (e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking)) != cudaSuccess ||
@@ -722,7 +773,11 @@ dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stre
       (e = cudaMalloc((void**)&c->flags, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->iters, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->upd, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&c->misc, sizeof(double2) * 4096)) != cudaSuccess) {
+      (e = cudaMalloc((void**)&c->misc, sizeof(double2) * 4096)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->partial, sizeof(double) * DL_MAXC * (((size_t)c->Vh * DL_MAXC + 255) / 256 + 8))) !=
+          cudaSuccess ||
+      (e = cudaMalloc((void**)&c->loopctr, 2 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->waitc, DL_NCMAX * sizeof(int))) != cudaSuccess) {
     dl_destroy(c);
     return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
   }
@@ -746,7 +801,7 @@ void dl_destroy(dl_ctx* c) {
   }
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
-  void* ptrs[] = {c->g64, c->g32, c->g16, c->partial, c->S, c->active, c->flags, c->iters, c->upd, c->misc, c->mom,
+  void* ptrs[] = {c->waitc, c->loopctr, c->g64, c->g32, c->g16, c->partial, c->S, c->active, c->flags, c->iters, c->upd, c->misc, c->mom,
                   c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -930,45 +985,38 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
   if (rs < 0) return rs;
   CK(dl::unpack(B, hi, 0, sol, xe->ref(), dtype, c->st));
   CK(dl::unpack(B, hi, 1, sol, po->ref(), dtype, c->st));
-  // true residual |b - M psi| / |b| on the full lattice, in FP64
+  // true residual |b - M psi| / |b| on the full lattice, in the solve's high
+  // precision with FP64 reductions
   {
-    Field *pe64, *po64, *be64, *bo64, *re, *ro;
-    if ((s = ensure_field(c, "tr_pe", P64, n, &pe64)) || (s = ensure_field(c, "tr_po", P64, n, &po64)) ||
-        (s = ensure_field(c, "tr_be", P64, n, &be64)) || (s = ensure_field(c, "tr_bo", P64, n, &bo64)) ||
-        (s = ensure_field(c, "tr_re", P64, n, &re)) || (s = ensure_field(c, "tr_ro", P64, n, &ro)))
+    Field *bh_e, *bh_o, *re, *ro;
+    if ((s = ensure_field(c, "tr_be", hi, n, &bh_e)) || (s = ensure_field(c, "tr_bo", hi, n, &bh_o)) ||
+        (s = ensure_field(c, "tr_re", hi, n, &re)) || (s = ensure_field(c, "tr_ro", hi, n, &ro)))
       return s;
-    CK(dl::copy(B, P64, hi, pe64->ref(), xe->ref(), nullptr, c->st));
-    CK(dl::copy(B, P64, hi, po64->ref(), po->ref(), nullptr, c->st));
-    CK(dl::pack(B, P64, 0, be64->ref(), src, dtype, c->st));
-    CK(dl::pack(B, P64, 1, bo64->ref(), src, dtype, c->st));
+    CK(dl::pack(B, hi, 0, bh_e->ref(), src, dtype, c->st));
+    CK(dl::pack(B, hi, 1, bh_o->ref(), src, dtype, c->st));
     GaugeSet g{c->g64, c->g32, c->g16};
     EpiSet E = epi(c, -c->kappa, 0, 0, 1, prm->flavour);
-    CK(dl::dslash(B, P64, 18, EPI_AUX, false, 0, po64->ref(), pe64->ref(), re->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
-                  nullptr, c->st));
-    CK(dl::dslash(B, P64, 18, EPI_AUX, false, 1, pe64->ref(), po64->ref(), ro->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
-                  nullptr, c->st));
+    CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, po->ref(), xe->ref(), re->ref(), g, E, nullptr, nullptr, NOF,
+                  NOF, NOF, nullptr, c->st));
+    CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 1, xe->ref(), po->ref(), ro->ref(), g, E, nullptr, nullptr, NOF,
+                  NOF, NOF, nullptr, c->st));
     std::vector<double> S(DL_NS * DL_NCMAX);
     double num[DL_MAX_RHS] = {0}, den[DL_MAX_RHS] = {0};
-    CK(dl::xmy_norm(B, P64, re->ref(), be64->ref(), re->ref(), nullptr, c->partial, c->st));
-    CK(colsum(c, B, DL_S_TMP));
-    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < n; ++i) num[i] += S[DL_S_TMP * DL_NCMAX + i];
-    CK(dl::xmy_norm(B, P64, ro->ref(), bo64->ref(), ro->ref(), nullptr, c->partial, c->st));
-    CK(colsum(c, B, DL_S_TMP));
-    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < n; ++i) num[i] += S[DL_S_TMP * DL_NCMAX + i];
-    CK(dl::norm2(B, P64, be64->ref(), nullptr, c->partial, c->st));
-    CK(colsum(c, B, DL_S_TMP));
-    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < n; ++i) den[i] += S[DL_S_TMP * DL_NCMAX + i];
-    CK(dl::norm2(B, P64, bo64->ref(), nullptr, c->partial, c->st));
-    CK(colsum(c, B, DL_S_TMP));
-    CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    for (int i = 0; i < n; ++i) den[i] += S[DL_S_TMP * DL_NCMAX + i];
+    auto col_sum = [&](double* acc) -> dl_status {
+      CK(colsum(c, B, DL_S_TMP));
+      CK(cudaMemcpyAsync(S.data(), c->S, sizeof(double) * DL_NS * DL_NCMAX, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      for (int i = 0; i < n; ++i) acc[i] += S[DL_S_TMP * DL_NCMAX + i];
+      return DL_OK;
+    };
+    CK(dl::xmy_norm(B, hi, re->ref(), bh_e->ref(), re->ref(), nullptr, c->partial, c->st));
+    if ((s = col_sum(num)) != DL_OK) return s;
+    CK(dl::xmy_norm(B, hi, ro->ref(), bh_o->ref(), ro->ref(), nullptr, c->partial, c->st));
+    if ((s = col_sum(num)) != DL_OK) return s;
+    CK(dl::norm2(B, hi, bh_e->ref(), nullptr, c->partial, c->st));
+    if ((s = col_sum(den)) != DL_OK) return s;
+    CK(dl::norm2(B, hi, bh_o->ref(), nullptr, c->partial, c->st));
+    if ((s = col_sum(den)) != DL_OK) return s;
     for (int i = 0; i < n; ++i) st.true_resid[i] = den[i] > 0 ? sqrt(num[i] / den[i]) : 0.0;
   }
   if (stats) *stats = st;
@@ -990,6 +1038,7 @@ dl_status dl_profile(dl_ctx* c, int enable, double* out) {
   if (enable >= 0) {
     if ((enable != 0) != (c->profiling != 0)) invalidate_graphs(c);
     c->profiling = enable != 0;
+    c->prof_pending[0] = c->prof_pending[1] = c->prof_pending[2] = c->profiling;
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
     memset(c->prof_n, 0, sizeof(c->prof_n));
     memset(c->prof_items, 0, sizeof(c->prof_items));
@@ -1082,6 +1131,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
   if (prm->hpe && prm->with_deriv) return fail(c, DL_ERR_ARG, "dl_tsm_run: the HPE estimator is local only");
   if ((s = enter(c)) != DL_OK) return s;
   auto t_all = std::chrono::steady_clock::now();
+  if (c->profiling) c->prof_pending[0] = c->prof_pending[1] = c->prof_pending[2] = 1;
   if ((s = ensure_momenta(c, prm->p2max)) != DL_OK) return s;
   const int np = c->np, nd = prm->with_deriv ? 5 : 1, T = c->dims[3];
   const int n_est = prm->hpe ? 3 : 2;

@@ -65,7 +65,7 @@ __global__ void xmy_norm_kernel(Batch B, FieldRef r, FieldRef b, FieldRef a, con
     }
     SIO<P>::store(seg_ptr_w<P>(r, L), seg_norm(r, L), nitems, j, bv);
   }
-  block_reduce_cols(red, npad, partial);
+  block_reduce_cols(red, npad, partial, B.pstride);
 }
 
 // partial |v|^2 per column
@@ -79,7 +79,7 @@ __global__ void norm_kernel(Batch B, FieldRef v, const int* mask, double* partia
 #pragma unroll
     for (int m = 0; m < 24; ++m) red += (double)a[m] * (double)a[m];
   }
-  block_reduce_cols(red, npad, partial);
+  block_reduce_cols(red, npad, partial, B.pstride);
 }
 
 // p = r + beta p
@@ -133,7 +133,7 @@ __global__ void sum_partials_kernel(Batch B, const double* __restrict__ partial,
   double acc = 0.0;
   if (l >= 0)
     for (int b = B.blk_begin[l] + threadIdx.x; b < B.blk_begin[l + 1]; b += blockDim.x)
-      acc += partial[(size_t)b * DL_MAXC + col];
+      acc += partial[(size_t)col * B.pstride + b];
   s[threadIdx.x] = acc;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -183,9 +183,42 @@ __global__ void cg_beta_kernel(int ncols, double* S, int* active, int* flags, in
 }
 #undef SV
 
+// Loop condition of the solver's graph: continue while some column is active
+// and this launch has run fewer than *limit iterations, unless reliable updates
+// are due: the loop stops when at least half of the active columns wait for
+// one, or one has waited 16 iterations, so that updates are done in batches
+// (each update applies the high-precision operator to every waiting column).
+__global__ void cg_cond_kernel(int ncols, const int* __restrict__ active, const int* __restrict__ flags, int* counter,
+                               const int* limit, int* wait, cudaGraphConditionalHandle h) {
+  const int gc = threadIdx.x;
+  const int a = (gc < ncols) && active[gc] != 0;
+  const int u = a && (flags[gc] & DL_FLAG_UPDATE) != 0;
+  int w = 0;
+  if (u) {
+    w = wait[gc] + 1;
+    wait[gc] = w;
+  }
+  const int n_a = __syncthreads_count(a);
+  const int n_u = __syncthreads_count(u);
+  const int old = __syncthreads_or(w >= 16);
+  if (threadIdx.x == 0) {
+    const int n = *counter + 1;
+    *counter = n;
+    const bool due = n_u > 0 && (2 * n_u >= n_a || old);
+    cudaGraphSetConditional(h, (n_a > 0 && !due && n < *limit) ? 1u : 0u);
+  }
+}
+
 }  // namespace
 
 namespace dl {
+
+cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter, const int* limit, int* wait,
+                    cudaGraphConditionalHandle h, cudaStream_t st) {
+  DL_COUNT();
+  cg_cond_kernel<<<1, DL_NCMAX, 0, st>>>(ncols, active, flags, counter, limit, wait, h);
+  return cudaGetLastError();
+}
 
 static int grid_of(Batch& B) { return blocks_for(B, 256); }
 

@@ -16,6 +16,136 @@
 
 namespace {
 
+// Epilogue shared by both thread mappings: acc holds D in (not yet scaled).
+template <int P, int EPI, typename R>
+__device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDesc& L, long long nitems, long long j,
+                                           int col, const FieldRef& aux, const FieldRef& out, const FieldRef& cr,
+                                           const FieldRef& cy, const FieldRef& cp, const double* alpha) {
+  double red = 0.0;
+  const R c = (R)e.c;
+#pragma unroll
+  for (int m = 0; m < 24; ++m) acc[m] *= c;
+  R v[24];
+  if (EPI != EPI_PLAIN) {
+    SIO<P>::load(seg_ptr<P>(aux, L), seg_norm(aux, L), nitems, j, v);
+    twist_apply<R>(v, (R)e.a2, (R)e.b2);
+#pragma unroll
+    for (int m = 0; m < 24; ++m) acc[m] += v[m];
+  }
+  if (EPI == EPI_CG) {
+    const R al = (R)alpha[L.rhs_base + col];
+    SIO<P>::load(seg_ptr<P>(cr, L), seg_norm(cr, L), nitems, j, v);  // r
+#pragma unroll
+    for (int m = 0; m < 24; ++m) {
+      v[m] -= al * acc[m];
+      red += (double)v[m] * (double)v[m];
+    }
+    SIO<P>::store(seg_ptr_w<P>(cr, L), seg_norm(cr, L), nitems, j, v);
+    SIO<P>::load(seg_ptr<P>(cp, L), seg_norm(cp, L), nitems, j, acc);  // p (Ap no longer needed)
+    SIO<P>::load(seg_ptr<P>(cy, L), seg_norm(cy, L), nitems, j, v);    // y
+#pragma unroll
+    for (int m = 0; m < 24; ++m) v[m] += al * acc[m];
+    SIO<P>::store(seg_ptr_w<P>(cy, L), seg_norm(cy, L), nitems, j, v);
+  } else {
+    twist_apply<R>(acc, (R)e.a1, (R)e.b1);
+    if (EPI == EPI_AUX_NORM) {
+#pragma unroll
+      for (int m = 0; m < 24; ++m) red += (double)acc[m] * (double)acc[m];
+    }
+    SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, acc);
+  }
+  return red;
+}
+
+// Neighbour of site (x,y,z,t) along direction d = 2 mu + (1 if backward): its
+// checkerboard index, and whether the hop crosses the time boundary.
+__device__ __forceinline__ int neighbour(const LatDesc& L, int x, int y, int z, int t, int d, bool& crosses) {
+  const int mu = d >> 1;
+  const bool bwd = d & 1;
+  crosses = false;
+  if (mu == 0) x = bwd ? (x == 0 ? L.X - 1 : x - 1) : (x + 1 == L.X ? 0 : x + 1);
+  else if (mu == 1) y = bwd ? (y == 0 ? L.Y - 1 : y - 1) : (y + 1 == L.Y ? 0 : y + 1);
+  else if (mu == 2) z = bwd ? (z == 0 ? L.Z - 1 : z - 1) : (z + 1 == L.Z ? 0 : z + 1);
+  else {
+    crosses = bwd ? (t == 0) : (t + 1 == L.T);
+    t = bwd ? (t == 0 ? L.T - 1 : t - 1) : (t + 1 == L.T ? 0 : t + 1);
+  }
+  return lex_of(L, x, y, z, t) >> 1;
+}
+
+// Staged mapping (npad >= 4): a CTA of 256 threads covers S = 256 / npad sites.
+// Phase A: 8 S threads each load and reconstruct one link (with the boundary
+// sign folded in) and the neighbour index into shared memory.  Phase B: thread
+// (site, column) applies the eight hops reading links from shared memory
+// (broadcast to the columns of a site) and the neighbour spinors from global memory.
+#ifndef DL_MINB
+#define DL_MINB 4  // resident CTAs per SM the staged stencil is compiled for (best of 2, 3, 4 measured)
+#endif
+
+template <int P, int G, int EPI>
+__global__ void __launch_bounds__(256, DL_MINB) dslash_staged(Batch B, int out_parity, float sgn_fwd, FieldRef in,
+                                                          FieldRef aux, FieldRef out, const void* __restrict__ gbase,
+                                                          EpiSet ep, const int* __restrict__ active,
+                                                          double* __restrict__ partial, FieldRef cr, FieldRef cy,
+                                                          FieldRef cp, const double* __restrict__ alpha) {
+  typedef typename SIO<P>::real R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int l = find_lat(B, blockIdx.x);
+  const LatDesc& L = B.lat[l];
+  const int lg = L.lognpad;
+  const int S = 256 >> lg;
+  const long long item0 = (long long)(blockIdx.x - B.blk_begin[l]) * 256;
+  const int site0 = (int)(item0 >> lg);
+  R* su = (R*)smem_raw;               // [8][S][18]
+  int* snb = (int*)(su + 8 * S * 18);  // [8][S]
+  const int p = out_parity, q = 1 - p;
+  const void* gb = gauge_seg<G>(gbase, L);
+  for (int task = threadIdx.x; task < 8 * S; task += 256) {
+    const int sl = task % S, d = task / S;
+    const int i = site0 + sl;
+    if (i < L.Vh) {
+      int x, y, z, t;
+      cb_coords(L, i, p, x, y, z, t);
+      bool crosses;
+      const int nb = neighbour(L, x, y, z, t, d, crosses);
+      R u[18];
+      GIO<G>::load(gb, L.Vh, (d & 1) ? q : p, d >> 1, (d & 1) ? nb : i, u);
+      const R f = crosses ? (R)L.tbc : (R)1;
+      R* dst = su + (d * S + sl) * 18;
+#pragma unroll
+      for (int e = 0; e < 18; ++e) dst[e] = u[e] * f;
+      snb[d * S + sl] = nb;
+    }
+  }
+  __syncthreads();
+  const long long nitems = (long long)L.Vh << lg;
+  const long long j = item0 + threadIdx.x;
+  const int col = threadIdx.x & ((1 << lg) - 1);
+  const int sl = threadIdx.x >> lg;
+  const bool act = (j < nitems) && (col < L.ncol) && (active == nullptr || active[L.rhs_base + col] != 0);
+  double red = 0.0;
+  if (act) {
+    const void* inb = seg_ptr<P>(in, L);
+    const float* inn = seg_norm(in, L);
+    const R sf = (R)sgn_fwd, sb = -(R)sgn_fwd;
+    R acc[24];
+#pragma unroll
+    for (int m = 0; m < 24; ++m) acc[m] = 0;
+#define HOP(D, MU, BWD)                                                                                  \
+    {                                                                                                    \
+      R v[24];                                                                                           \
+      SIO<P>::load(inb, inn, nitems, ((long long)snb[(D) * S + sl] << lg) + col, v);                     \
+      hop_term<R, BWD, MU>(acc, v, su + ((D) * S + sl) * 18, BWD ? sb : sf);                             \
+    }
+    HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
+    HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
+#undef HOP
+    red = epilogue<P, EPI, R>(acc, ep.e[l], L, nitems, j, col, aux, out, cr, cy, cp, alpha);
+  }
+  if (EPI == EPI_AUX_NORM || EPI == EPI_CG) block_reduce_cols(red, 1 << lg, partial, B.pstride);
+}
+
+// Direct mapping (npad < 4): every thread computes its own neighbours and links.
 template <int P, int G, int EPI>
 __global__ void __launch_bounds__(256) dslash_kernel(Batch B, int out_parity, float sgn_fwd, FieldRef in, FieldRef aux,
                                                      FieldRef out, const void* __restrict__ gbase, EpiSet ep,
@@ -43,95 +173,48 @@ __global__ void __launch_bounds__(256) dslash_kernel(Batch B, int out_parity, fl
     R acc[24];
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] = 0;
-    R v[24], u[18];
-    // x direction
-    {
-      int nb = lex_of(L, (x + 1 == L.X) ? 0 : x + 1, y, z, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, p, 0, i, u);
-      hop_term<R, false, 0>(acc, v, u, sf);
-      nb = lex_of(L, (x == 0) ? L.X - 1 : x - 1, y, z, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, q, 0, nb, u);
-      hop_term<R, true, 0>(acc, v, u, sb);
+#define HOP(D, MU, BWD)                                                                  \
+    {                                                                                    \
+      bool crosses;                                                                      \
+      const int nb = neighbour(L, x, y, z, t, D, crosses);                               \
+      R v[24], u[18];                                                                    \
+      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);             \
+      GIO<G>::load(gb, L.Vh, BWD ? q : p, MU, BWD ? nb : i, u);                           \
+      if (crosses) {                                                                     \
+        _Pragma("unroll") for (int m = 0; m < 24; ++m) v[m] *= (R)L.tbc;                 \
+      }                                                                                  \
+      hop_term<R, BWD, MU>(acc, v, u, BWD ? sb : sf);                                    \
     }
-    // y direction
-    {
-      int nb = lex_of(L, x, (y + 1 == L.Y) ? 0 : y + 1, z, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, p, 1, i, u);
-      hop_term<R, false, 1>(acc, v, u, sf);
-      nb = lex_of(L, x, (y == 0) ? L.Y - 1 : y - 1, z, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, q, 1, nb, u);
-      hop_term<R, true, 1>(acc, v, u, sb);
-    }
-    // z direction
-    {
-      int nb = lex_of(L, x, y, (z + 1 == L.Z) ? 0 : z + 1, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, p, 2, i, u);
-      hop_term<R, false, 2>(acc, v, u, sf);
-      nb = lex_of(L, x, y, (z == 0) ? L.Z - 1 : z - 1, t) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      GIO<G>::load(gb, L.Vh, q, 2, nb, u);
-      hop_term<R, true, 2>(acc, v, u, sb);
-    }
-    // t direction, with the boundary factor on hops across t = T-1 <-> 0
-    {
-      const R bc = (R)L.tbc;
-      int nb = lex_of(L, x, y, z, (t + 1 == L.T) ? 0 : t + 1) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      if (t + 1 == L.T) {
-#pragma unroll
-        for (int m = 0; m < 24; ++m) v[m] *= bc;
-      }
-      GIO<G>::load(gb, L.Vh, p, 3, i, u);
-      hop_term<R, false, 3>(acc, v, u, sf);
-      nb = lex_of(L, x, y, z, (t == 0) ? L.T - 1 : t - 1) >> 1;
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);
-      if (t == 0) {
-#pragma unroll
-        for (int m = 0; m < 24; ++m) v[m] *= bc;
-      }
-      GIO<G>::load(gb, L.Vh, q, 3, nb, u);
-      hop_term<R, true, 3>(acc, v, u, sb);
-    }
-    const Epi e = ep.e[l];
-    const R c = (R)e.c;
-#pragma unroll
-    for (int m = 0; m < 24; ++m) acc[m] *= c;
-    if (EPI != EPI_PLAIN) {
-      SIO<P>::load(seg_ptr<P>(aux, L), seg_norm(aux, L), nitems, j, v);
-      twist_apply<R>(v, (R)e.a2, (R)e.b2);
-#pragma unroll
-      for (int m = 0; m < 24; ++m) acc[m] += v[m];
-    }
-    if (EPI == EPI_CG) {
-      const R al = (R)alpha[L.rhs_base + col];
-      R w[24];
-      SIO<P>::load(seg_ptr<P>(cp, L), seg_norm(cp, L), nitems, j, w);   // p
-      SIO<P>::load(seg_ptr<P>(cy, L), seg_norm(cy, L), nitems, j, v);   // y
-#pragma unroll
-      for (int m = 0; m < 24; ++m) v[m] += al * w[m];
-      SIO<P>::store(seg_ptr_w<P>(cy, L), seg_norm(cy, L), nitems, j, v);
-      SIO<P>::load(seg_ptr<P>(cr, L), seg_norm(cr, L), nitems, j, v);   // r
-#pragma unroll
-      for (int m = 0; m < 24; ++m) {
-        v[m] -= al * acc[m];
-        red += (double)v[m] * (double)v[m];
-      }
-      SIO<P>::store(seg_ptr_w<P>(cr, L), seg_norm(cr, L), nitems, j, v);
-    } else {
-      twist_apply<R>(acc, (R)e.a1, (R)e.b1);
-      if (EPI == EPI_AUX_NORM) {
-#pragma unroll
-        for (int m = 0; m < 24; ++m) red += (double)acc[m] * (double)acc[m];
-      }
-      SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, acc);
-    }
+    HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
+    HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
+#undef HOP
+    red = epilogue<P, EPI, R>(acc, ep.e[l], L, nitems, j, col, aux, out, cr, cy, cp, alpha);
   }
-  if (EPI == EPI_AUX_NORM || EPI == EPI_CG) block_reduce_cols(red, 1 << L.lognpad, partial);
+  if (EPI == EPI_AUX_NORM || EPI == EPI_CG) block_reduce_cols(red, 1 << L.lognpad, partial, B.pstride);
+}
+
+template <int P, int G, int EPI>
+cudaError_t launch_epi(const Batch& B, int grid, float sgn, int op, FieldRef in, FieldRef aux, FieldRef out,
+                       const void* g, const EpiSet& ep, const int* active, double* partial, FieldRef cr, FieldRef cy,
+                       FieldRef cp, const double* alpha, cudaStream_t st) {
+  int minlg = 31;
+  for (int l = 0; l < B.nlat; ++l) minlg = B.lat[l].lognpad < minlg ? B.lat[l].lognpad : minlg;
+  if (minlg >= 2) {
+    typedef typename SIO<P>::real R;
+    const int S = 256 >> minlg;
+    const size_t smem = (size_t)8 * S * 18 * sizeof(R) + (size_t)8 * S * sizeof(int);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(dslash_staged<P, G, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 64 * 18 * 8 + 8 * 64 * 4);
+      attr_set = true;
+    }
+    DL_COUNT();
+    dslash_staged<P, G, EPI><<<grid, 256, smem, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
+  } else {
+    DL_COUNT();
+    dslash_kernel<P, G, EPI><<<grid, 256, 0, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
+  }
+  return cudaGetLastError();
 }
 
 template <int P, int G>
@@ -140,25 +223,16 @@ cudaError_t launch_pg(const Batch& B, int grid, int epi, float sgn, int op, Fiel
                       FieldRef cp, const double* alpha, cudaStream_t st) {
   switch (epi) {
     case EPI_PLAIN:
-      DL_COUNT();
-      dslash_kernel<P, G, EPI_PLAIN><<<grid, 256, 0, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
-      break;
+      return launch_epi<P, G, EPI_PLAIN>(B, grid, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
     case EPI_AUX:
-      DL_COUNT();
-      dslash_kernel<P, G, EPI_AUX><<<grid, 256, 0, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
-      break;
+      return launch_epi<P, G, EPI_AUX>(B, grid, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
     case EPI_AUX_NORM:
-      DL_COUNT();
-      dslash_kernel<P, G, EPI_AUX_NORM><<<grid, 256, 0, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
-      break;
+      return launch_epi<P, G, EPI_AUX_NORM>(B, grid, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
     case EPI_CG:
-      DL_COUNT();
-      dslash_kernel<P, G, EPI_CG><<<grid, 256, 0, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
-      break;
+      return launch_epi<P, G, EPI_CG>(B, grid, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
     default:
       return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace

@@ -5,20 +5,20 @@
 //     item j = site*npad + column, npad = 2^lognpad >= active columns.
 //     F64: 12 chunks of double2 (one complex each, m = 3*spin + colour)
 //     F32:  6 chunks of float4  (complex 2k, 2k+1)
-//     F16:  3 chunks of uint4   (8 halves = complex 4k..4k+3) + float norm[item]
-//           (values are stored divided by the item's max |re|,|im|)
+//     16-bit: 3 chunks of uint4 (8 x 16 bit = complex 4k..4k+3) + float norm[item];
+//           fixed point, value = q * norm / 32767 with norm the item's max |re|,|im|,
+//           q stored offset-binary (q + 32768)
 //   gauge field, per lattice: chunk k of link (parity p, mu, site i) at
 //     base + ((p*4 + mu)*GK + k)*Vh + i
 //     F64 recon 18: 9 double2 (row-major complex entries)
 //     F32 recon 12: 3 float4  (rows 0 and 1), row 2 = conj(row0 x row1)
 //     F32 recon  8: 2 float4  (a1, a2, b0, arg a0, arg c0)
-//     F16 recon 12: 3 uint2   (rows 0 and 1 as halves)
-//     F16 recon  8: 1 uint4   (a1, a2, b0, arg a0 / pi, arg c0 / pi)
+//     16-bit recon 12: 3 uint2 (rows 0 and 1, int16 fixed point q / 32767)
+//     16-bit recon  8: 1 uint4 (a1, a2, b0, arg a0 / pi, arg c0 / pi as int16 fixed point)
 // Several lattices can share one launch ("batch"): lattice l owns blocks
 // [blk_begin_l, blk_begin_{l+1}) and its own segment of every field.
 #pragma once
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -44,6 +44,7 @@ struct LatDesc {
 
 struct Batch {
   int nlat;
+  int pstride;  // column stride of the partial-sum buffer (>= blocks of any launch)
   int blk_begin[DL_MAX_LAT + 1];
   LatDesc lat[DL_MAX_LAT];
 };
@@ -115,21 +116,39 @@ template <> struct SIO<P32> {
   }
 };
 
+// 16-bit storage: 16-bit fixed point scaled by the item's max |re|,|im|
+// (value = q * norm / 32767, q in [-32767, 32767]), i.e. 15 bits of precision
+// relative to the site.  q is stored offset by 32768 (u = q + 32768) so that
+// decoding is one byte permute into the mantissa of 2^23 + u followed by an
+// exact subtraction, and encoding is one fused multiply-add whose result's low
+// 16 mantissa bits are u (round to nearest even) followed by a byte permute.
+__device__ __forceinline__ float u16lo_to_q(unsigned w) {
+  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7610)) - 8421376.0f;  // (2^23 + u) - (2^23 + 32768)
+}
+__device__ __forceinline__ float u16hi_to_q(unsigned w) {
+  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7632)) - 8421376.0f;
+}
+// pack round(a), round(b) (|a|,|b| <= 32767) as offset-binary 16-bit pair
+__device__ __forceinline__ unsigned q_to_u16pair(float a, float b) {
+  const unsigned ua = (unsigned)__float_as_int(a + 8421376.0f);
+  const unsigned ub = (unsigned)__float_as_int(b + 8421376.0f);
+  return __byte_perm(ua, ub, 0x5410);
+}
+
 template <> struct SIO<P16> {
   typedef float real;
   static constexpr int K = 3;
   __device__ static __forceinline__ void load(const void* b, const float* nrm, long long st, long long j, float v[24]) {
     const uint4* p = (const uint4*)b;
-    float s = __ldg(nrm + j);
+    const float s = __ldg(nrm + j) * (1.0f / 32767.0f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint4 c = __ldg(p + k * st + j);
-      const __half2* h = reinterpret_cast<const __half2*>(&c);
+      const unsigned w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        float2 f = __half22float2(h[q]);
-        v[8 * k + 2 * q] = f.x * s;
-        v[8 * k + 2 * q + 1] = f.y * s;
+        v[8 * k + 2 * q] = u16lo_to_q(w[q]) * s;
+        v[8 * k + 2 * q + 1] = u16hi_to_q(w[q]) * s;
       }
     }
   }
@@ -138,15 +157,14 @@ template <> struct SIO<P16> {
     float m = 0.f;
 #pragma unroll
     for (int q = 0; q < 24; ++q) m = fmaxf(m, fabsf(v[q]));
-    float inv = m > 0.f ? 1.0f / m : 0.f;
+    const float sc = m > 0.f ? 32767.0f / m : 0.f;
     nrm[j] = m;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint4 c;
-      __half2* h = reinterpret_cast<__half2*>(&c);
+      unsigned w[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(v[8 * k + 2 * q] * inv, v[8 * k + 2 * q + 1] * inv);
-      p[k * st + j] = c;
+      for (int q = 0; q < 4; ++q) w[q] = q_to_u16pair(v[8 * k + 2 * q] * sc, v[8 * k + 2 * q + 1] * sc);
+      p[k * st + j] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 };
@@ -264,18 +282,22 @@ template <> struct GIO<G32R8> {
     recon8(c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, u);
   }
 };
+// 16-bit links: fixed point q / 32767 stored offset by 32768 like the spinors
+// (entries of an SU(3) matrix lie in [-1, 1]; recon-8 angles are stored / pi).
 template <> struct GIO<G16R12> {
   typedef float real;
   static constexpr int GK = 3;
   typedef uint2 chunk;
   __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
     const uint2* g = (const uint2*)b + (size_t)((p * 4 + mu) * 3) * Vh + i;
+    const float s = 1.0f / 32767.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint2 c = __ldg(g + (size_t)k * Vh);
-      const __half2* h = reinterpret_cast<const __half2*>(&c);
-      float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]);
-      u[4 * k] = f0.x; u[4 * k + 1] = f0.y; u[4 * k + 2] = f1.x; u[4 * k + 3] = f1.y;
+      u[4 * k] = u16lo_to_q(c.x) * s;
+      u[4 * k + 1] = u16hi_to_q(c.x) * s;
+      u[4 * k + 2] = u16lo_to_q(c.y) * s;
+      u[4 * k + 3] = u16hi_to_q(c.y) * s;
     }
     recon12(u);
   }
@@ -287,10 +309,9 @@ template <> struct GIO<G16R8> {
   __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, float u[18]) {
     const uint4* g = (const uint4*)b + (size_t)((p * 4 + mu)) * Vh + i;
     uint4 c = __ldg(g);
-    const __half2* h = reinterpret_cast<const __half2*>(&c);
-    float2 f0 = __half22float2(h[0]), f1 = __half22float2(h[1]), f2 = __half22float2(h[2]), f3 = __half22float2(h[3]);
-    const float pi = 3.14159265358979f;
-    recon8(f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x * pi, f3.y * pi, u);
+    const float s = 1.0f / 32767.0f, pi = 3.14159265358979f;
+    recon8(u16lo_to_q(c.x) * s, u16hi_to_q(c.x) * s, u16lo_to_q(c.y) * s, u16hi_to_q(c.y) * s, u16lo_to_q(c.z) * s,
+           u16hi_to_q(c.z) * s, u16lo_to_q(c.w) * s * pi, u16hi_to_q(c.w) * s * pi, u);
   }
 };
 
@@ -383,8 +404,9 @@ __device__ __forceinline__ void twist_apply(R v[24], R a, R b) {
 
 // Per-column block reduction (deterministic).  Each thread contributes val for
 // column col = (its item index) & (npad-1); blockDim.x is a multiple of 32 and
-// npad <= 32.  Writes partial[blockIdx.x * DL_MAXC + col] for col < npad.
-__device__ __forceinline__ void block_reduce_cols(double val, int npad, double* partial) {
+// npad <= 32.  Writes partial[col * pstride + blockIdx.x] for col < npad
+// (column-major, so the final per-column sum reads contiguous memory).
+__device__ __forceinline__ void block_reduce_cols(double val, int npad, double* partial, int pstride) {
   __shared__ double sred[32][DL_MAXC];
   for (int off = 16; off >= npad; off >>= 1) val += __shfl_xor_sync(0xffffffffu, val, off);
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -394,7 +416,7 @@ __device__ __forceinline__ void block_reduce_cols(double val, int npad, double* 
     double s = 0.0;
     int nw = blockDim.x >> 5;
     for (int w = 0; w < nw; ++w) s += sred[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * DL_MAXC + threadIdx.x] = s;
+    partial[(size_t)threadIdx.x * pstride + blockIdx.x] = s;
   }
 }
 

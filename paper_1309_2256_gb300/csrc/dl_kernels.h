@@ -33,6 +33,8 @@ cudaError_t sum_partials(const Batch& B, const double* partial, double* out, int
                          cudaStream_t st);
 cudaError_t cg_alpha(int ncols, double* S, int* active, int* flags, cudaStream_t st);
 cudaError_t cg_beta(int ncols, double* S, int* active, int* flags, int* iters, double tol2, double delta, cudaStream_t st);
+cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter, const int* limit, int* wait,
+                    cudaGraphConditionalHandle h, cudaStream_t st);
 
 // layout (single-lattice batches)
 cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void* natural, int dtype, cudaStream_t st);
@@ -46,7 +48,9 @@ cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, voi
 cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                            FieldRef eta_o, const void* g64, double2* W, cudaStream_t st);
 cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
-                     cudaStream_t st);
+                     int fp32, cudaStream_t st);
+cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+                       FieldRef eta_o, const void* g64, int mx, double2* G1, cudaStream_t st);
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
                               const double2* G3, double pre_re, double pre_im, double2* out, int accumulate,
                               cudaStream_t st);

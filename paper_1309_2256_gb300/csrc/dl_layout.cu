@@ -163,25 +163,22 @@ __global__ void pack_gauge_kernel(LatDesc L, const double2* __restrict__ links, 
       }
     }
     if (g16) {
+      // offset-binary 16-bit fixed point: u = round(x * 32767) + 32768
+      auto u16 = [](double x) -> unsigned {
+        double y = x * 32767.0;
+        y = y > 32767.0 ? 32767.0 : (y < -32767.0 ? -32767.0 : y);
+        return (unsigned)(__double2int_rn(y) + 32768);
+      };
+      auto pair = [&](double a, double b) -> unsigned { return u16(a) | (u16(b) << 16); };
       if (rec16 == 12) {
         uint2* g = (uint2*)g16;
-        for (int k = 0; k < 3; ++k) {
-          uint2 c;
-          __half2* h = reinterpret_cast<__half2*>(&c);
-          h[0] = __floats2half2_rn((float)e[2 * k].x, (float)e[2 * k].y);
-          h[1] = __floats2half2_rn((float)e[2 * k + 1].x, (float)e[2 * k + 1].y);
-          g[(blk * 3 + k) * Vh + i] = c;
-        }
+        for (int k = 0; k < 3; ++k)
+          g[(blk * 3 + k) * Vh + i] = make_uint2(pair(e[2 * k].x, e[2 * k].y), pair(e[2 * k + 1].x, e[2 * k + 1].y));
       } else {
         uint4* g = (uint4*)g16;
         const double ipi = 1.0 / 3.14159265358979323846;
-        uint4 c;
-        __half2* h = reinterpret_cast<__half2*>(&c);
-        h[0] = __floats2half2_rn((float)e[1].x, (float)e[1].y);
-        h[1] = __floats2half2_rn((float)e[2].x, (float)e[2].y);
-        h[2] = __floats2half2_rn((float)e[3].x, (float)e[3].y);
-        h[3] = __floats2half2_rn((float)(atan2(e[0].y, e[0].x) * ipi), (float)(atan2(e[6].y, e[6].x) * ipi));
-        g[blk * Vh + i] = c;
+        g[blk * Vh + i] = make_uint4(pair(e[1].x, e[1].y), pair(e[2].x, e[2].y), pair(e[3].x, e[3].y),
+                                     pair(atan2(e[0].y, e[0].x) * ipi, atan2(e[6].y, e[6].x) * ipi));
       }
     }
   }

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
 Tolerances: FP64 operators <= 1e-13 relative, FP32 <= 2e-6 (the bounds of the
-benchmark spec), FP16 storage <= 4e-3 (half mantissa with a per-site
-scale); noise and indexing bit-exact; loops from solves converged to CG residual
+benchmark spec), 16-bit storage <= 3e-4 (int16 fixed point with a
+per-site scale); noise and indexing bit-exact; loops from solves converged to CG residual
 1e-10 within 1e-8 of the dense-inverse loops.
 """
 import numpy as np
@@ -110,7 +110,7 @@ def test_operator_f64(dl, opcase, name, f):
 
 
 @pytest.mark.parametrize("name", ["M", "MHAT", "MHAT_DAG", "RECON", "BH"])
-@pytest.mark.parametrize("prec,recon,tol", [(1, 12, 2e-6), (1, 8, 2e-6), (2, 12, 4e-3), (2, 8, 4e-3)])
+@pytest.mark.parametrize("prec,recon,tol", [(1, 12, 2e-6), (1, 8, 2e-6), (2, 12, 3e-4), (2, 8, 3e-4)])
 def test_operator_low_precision(dl, opcase, name, prec, recon, tol):
     dims, links, x, aux = opcase
     kappa, amu = 0.161, 0.0055
@@ -169,7 +169,7 @@ def test_solve_and_loops_tiny_config(dl):
 
 @pytest.mark.parametrize("lo,delta", [(1, 0.1), (2, 0.1)])
 def test_mixed_precision_solve(dl, lo, delta):
-    """FP32 / FP16 Krylov vectors with FP64 reliable updates reach 1e-10."""
+    """FP32 / 16-bit Krylov vectors with FP64 reliable updates reach 1e-10."""
     dims = (4, 4, 4, 8)
     kappa, amu = 0.161, 0.0055
     links = synth.gauge_links(dims, 0.4, 41)
@@ -196,12 +196,15 @@ def test_mixed_precision_solve(dl, lo, delta):
 
 @pytest.mark.parametrize("est", ["standard", "one_end", "gen_one_end", "hpe"])
 def test_contractions_with_momenta(dl, est):
-    dims = (4, 6, 4, 8)
+    """Bilinears, derivative bilinears and momentum projection against the oracle,
+    for s = M_u^-1 eta exactly (the generalised estimator uses D_W s = eta - 2 i k amu g5 s)."""
+    dims = (4, 6, 2, 4)
     kappa, amu = 0.161, 0.0055
     links = synth.gauge_links(dims, 0.4, 51)
     n = 3
     eta = np.stack([noise.z4_noise(dims, 52, r) for r in range(n)])
-    s = synth.gaussian_spinors(dims, n, 53)  # contraction parity does not need s = M^-1 eta
+    minv = np.linalg.inv(op.dense_matrix(links, kappa, amu, 1))
+    s = np.stack([(minv @ e.ravel()).reshape(e.shape) for e in eta])
     with_deriv = 0 if est == "hpe" else 1
     p2 = 4
     ctx = _ctx(dl, dims, links, kappa, amu)
@@ -218,11 +221,37 @@ def test_contractions_with_momenta(dl, est):
     for r in range(n):
         xi, phi = loops.pair(est, links, eta[r], s[r], kappa, amu)
         ref = pre * loops.project_momenta(loops.bilinear(xi, phi), dims, p2)
-        assert _rel(got[r, :, :, 0], ref) < 1e-12, (est, r)
+        assert _rel(got[r, :, :, 0], ref) < 1e-11, (est, r, _rel(got[r, :, :, 0], ref))
         if with_deriv:
             for mu in range(4):
                 refd = pre * loops.project_momenta(loops.derivative_bilinear(links, xi, phi, mu), dims, p2)
-                assert _rel(got[r, :, :, 1 + mu], refd) < 1e-12, (est, r, mu)
+                assert _rel(got[r, :, :, 1 + mu], refd) < 1e-11, (est, r, mu)
+
+
+def test_contraction_fp32_inputs(dl):
+    """complex64 inputs (the low-precision pipeline): FP32 products and DFT, within 1e-6."""
+    dims = (4, 6, 4, 8)
+    kappa, amu = 0.161, 0.0055
+    links = synth.gauge_links(dims, 0.4, 54)
+    n = 5
+    eta = np.stack([noise.z4_noise(dims, 55, r) for r in range(n)]).astype(np.complex64)
+    s = synth.gaussian_spinors(dims, n, 56).astype(np.complex64)
+    ctx = _ctx(dl, dims, links, kappa, amu)
+    try:
+        npm = len(dl.dl_momenta(4))
+        out = torch.zeros((n, dims[3], npm, 5, 4, 4), dtype=torch.complex128, device="cuda")
+        dl.dl_contract(ctx, dl.DL_EST_ONE_END, _dev(eta), _dev(s), n, dl.DL_C64, 1, 4, out)
+        got = out.cpu().numpy()
+    finally:
+        dl.dl_destroy(ctx)
+    pre = loops.prefactor("one_end", kappa, amu)
+    for r in range(n):
+        xi, phi = loops.pair("one_end", links, eta[r].astype(np.complex128), s[r].astype(np.complex128), kappa, amu)
+        ref = pre * loops.project_momenta(loops.bilinear(xi, phi), dims, 4)
+        assert _rel(got[r, :, :, 0], ref) < 1e-6
+        for mu in range(4):
+            refd = pre * loops.project_momenta(loops.derivative_bilinear(links, xi, phi, mu), dims, 4)
+            assert _rel(got[r, :, :, 1 + mu], refd) < 1e-6
 
 
 def test_hpe_exact_matches_oracle(dl):
