@@ -164,6 +164,158 @@ __global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, Field
   }
 }
 
+
+// Fused per-site bilinears and x-direction DFT.  One CTA per (t, z, y) row;
+// thread (x, column) forms the 16 (per derivative slot) components of its site
+// in R, stores them to shared memory, and the CTA then writes
+//   G1[comp][t][z][y][nx][col] = sum_x exp(-2 pi i nx x / X) C_comp(x, col).
+// Derivative slots d = 1..4 (mu = d - 1) are processed one at a time.
+template <int P, int MODE, bool DERIV, typename R>
+__global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+                                                           FieldRef eta_o, const double2* __restrict__ g64, int mx,
+                                                           int cwlog, double2* __restrict__ G1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const LatDesc& L = B.lat[0];
+  const int lg = L.lognpad, npad = 1 << lg;
+  const int cw = 1 << cwlog;                     // columns handled by this CTA
+  const int NX = 2 * mx + 1;
+  typedef struct { R x, y; } cr;
+  cr* cs = (cr*)smem_raw;                        // [16][X][cw]
+  cr* ph = cs + 16 * L.X * cw;                   // [X]
+  const int row = blockIdx.x;                    // (t * Z + z) * Y + y
+  const int y = row % L.Y, z = (row / L.Y) % L.Z, t = row / (L.Y * L.Z);
+  const int x = threadIdx.x >> cwlog, cl = threadIdx.x & (cw - 1);
+  const int col = blockIdx.y * cw + cl;
+  if (threadIdx.x < L.X) {
+    double sn, cn;
+    sincospi(2.0 * (double)threadIdx.x / (double)L.X, &sn, &cn);
+    ph[threadIdx.x].x = (R)cn;
+    ph[threadIdx.x].y = (R)(-sn);
+  }
+  const long long nitems = (long long)L.Vh << lg;
+  const int lex = lex_of(L, x, y, z, t);
+  const int p = (x + y + z + t) & 1;
+  const bool live = col < L.ncol;
+  double xi[24], phi[24];
+  if (live) make_pair<P, MODE>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, ((long long)(lex >> 1) << lg) + col, xi, phi);
+  const long long nrows = (long long)L.T * L.Z * L.Y;
+  const int nd = DERIV ? 5 : 1;
+  for (int d = 0; d < nd; ++d) {
+    R cre[16], cim[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) cre[k] = cim[k] = 0;
+    if (live) {
+      if (d == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              R xr = (R)xi[2 * (3 * a + c)], xim = (R)xi[2 * (3 * a + c) + 1];
+              R pr = (R)phi[2 * (3 * b + c)], pim = (R)phi[2 * (3 * b + c) + 1];
+              re += xr * pr + xim * pim;
+              im += xr * pim - xim * pr;
+            }
+            cre[4 * a + b] = re;
+            cim[4 * a + b] = im;
+          }
+      } else {
+        const int mu = d - 1;
+        int xn = x, yn = y, zn = z, tn = t;
+        double bc = 1.0;
+        if (mu == 0) xn = (x + 1 == L.X) ? 0 : x + 1;
+        if (mu == 1) yn = (y + 1 == L.Y) ? 0 : y + 1;
+        if (mu == 2) zn = (z + 1 == L.Z) ? 0 : z + 1;
+        if (mu == 3) {
+          tn = (t + 1 == L.T) ? 0 : t + 1;
+          if (t + 1 == L.T) bc = L.tbc;
+        }
+        const int lexn = lex_of(L, xn, yn, zn, tn);
+        double xif[24], phif[24];
+        make_pair<P, MODE>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, ((long long)(lexn >> 1) << lg) + col, xif, phif);
+        double u[18];
+        const double2* gl = g64 + (size_t)((p * 4 + mu) * 9) * L.Vh + (lex >> 1);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          double2 cc = gl[(size_t)k * L.Vh];
+          u[2 * k] = cc.x;
+          u[2 * k + 1] = cc.y;
+        }
+        R up[24], udp[24];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            R r1 = 0, i1 = 0, r2 = 0, i2 = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              R ur = (R)u[2 * (3 * a + b)], ui = (R)u[2 * (3 * a + b) + 1];
+              R vr = (R)(phif[2 * (3 * sp + b)] * bc), vi = (R)(phif[2 * (3 * sp + b) + 1] * bc);
+              r1 += ur * vr - ui * vi;
+              i1 += ur * vi + ui * vr;
+              R wr = (R)u[2 * (3 * b + a)], wi = -(R)u[2 * (3 * b + a) + 1];
+              R qr = (R)phi[2 * (3 * sp + b)], qi = (R)phi[2 * (3 * sp + b) + 1];
+              r2 += wr * qr - wi * qi;
+              i2 += wr * qi + wi * qr;
+            }
+            up[2 * (3 * sp + a)] = r1;
+            up[2 * (3 * sp + a) + 1] = i1;
+            udp[2 * (3 * sp + a)] = r2;
+            udp[2 * (3 * sp + a) + 1] = i2;
+          }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            R re = 0, im = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              R xr = (R)xi[2 * (3 * a + c)], xim = (R)xi[2 * (3 * a + c) + 1];
+              R pr = up[2 * (3 * b + c)], pim = up[2 * (3 * b + c) + 1];
+              re += xr * pr + xim * pim;
+              im += xr * pim - xim * pr;
+              R fr = (R)(xif[2 * (3 * a + c)] * bc), fim = (R)(xif[2 * (3 * a + c) + 1] * bc);
+              R qr = udp[2 * (3 * b + c)], qim = udp[2 * (3 * b + c) + 1];
+              re -= fr * qr + fim * qim;
+              im -= fr * qim - fim * qr;
+            }
+            cre[4 * a + b] = re;
+            cim[4 * a + b] = im;
+          }
+      }
+    }
+    __syncthreads();  // previous slot's DFT has finished reading cs
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      cs[(k * L.X + x) * cw + cl].x = cre[k];
+      cs[(k * L.X + x) * cw + cl].y = cim[k];
+    }
+    __syncthreads();
+    const int ntask = 16 * NX * cw;
+    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+      const int cc = task & (cw - 1);
+      const int kx = (task >> cwlog) % NX;
+      const int k = (task >> cwlog) / NX;
+      int n = kx - mx;
+      n = ((n % L.X) + L.X) % L.X;
+      R re = 0, im = 0;
+      int q = 0;
+      for (int xx = 0; xx < L.X; ++xx) {
+        const cr v = cs[(k * L.X + xx) * cw + cc];
+        const cr w = ph[q];
+        re += v.x * w.x - v.y * w.y;
+        im += v.x * w.y + v.y * w.x;
+        q += n;
+        if (q >= L.X) q -= L.X;
+      }
+      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] =
+          make_double2((double)re, (double)im);
+    }
+  }
+}
+
 __global__ void phase_kernel(int len, double2* ph) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= len) return;
@@ -172,31 +324,54 @@ __global__ void phase_kernel(int len, double2* ph) {
   ph[q] = make_double2(c, -s);  // exp(-2 pi i q / len)
 }
 
-// out[b][k][s] = sum_j in[b][j][s] exp(-2 pi i (k - m) j / len)
-__global__ void dft_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long nb, int len,
-                           long long stride, int m, const double2* __restrict__ ph) {
+// out[b][k][s] = sum_j in[b][j][s] exp(-2 pi i (k - m) j / len), accumulated in R.
+// One CTA per (b, tile of DL_DFT_TILE s): the [len x tile] input slab is staged
+// in shared memory with coalesced loads, then the CTA's threads compute the
+// (2m+1) x tile outputs from shared memory.
+#define DL_DFT_TILE 64
+template <typename R>
+__global__ void __launch_bounds__(256) dft_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long nb,
+                                                  int len, long long stride, int m, const double2* __restrict__ ph) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef struct { R x, y; } cr;
+  cr* slab = (cr*)smem_raw;            // [len][DL_DFT_TILE]
+  cr* phs = slab + len * DL_DFT_TILE;  // [len]
+  const long long ntile = (stride + DL_DFT_TILE - 1) / DL_DFT_TILE;
+  const long long b = blockIdx.x / ntile;
+  const long long s0 = (blockIdx.x % ntile) * DL_DFT_TILE;
+  const int tw = (int)((stride - s0) < DL_DFT_TILE ? (stride - s0) : DL_DFT_TILE);
+  for (int q = threadIdx.x; q < len; q += blockDim.x) {
+    phs[q].x = (R)ph[q].x;
+    phs[q].y = (R)ph[q].y;
+  }
+  const double2* src = in + b * len * stride + s0;
+  for (int e = threadIdx.x; e < len * DL_DFT_TILE; e += blockDim.x) {
+    const int j = e / DL_DFT_TILE, ss = e % DL_DFT_TILE;
+    if (ss < tw) {
+      const double2 v = src[(long long)j * stride + ss];
+      slab[e].x = (R)v.x;
+      slab[e].y = (R)v.y;
+    }
+  }
+  __syncthreads();
   const int nk = 2 * m + 1;
-  const long long tot = nb * nk * stride;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long s = idx % stride;
-    long long r = idx / stride;
-    int k = (int)(r % nk);
-    long long b = r / nk;
+  for (int o = threadIdx.x; o < nk * DL_DFT_TILE; o += blockDim.x) {
+    const int k = o / DL_DFT_TILE, ss = o % DL_DFT_TILE;
+    if (ss >= tw) continue;
     int n = k - m;
     n = ((n % len) + len) % len;
-    const double2* src = in + (b * len) * stride + s;
-    double re = 0.0, im = 0.0;
+    R re = 0, im = 0;
     int q = 0;
+#pragma unroll 4
     for (int jx = 0; jx < len; ++jx) {
-      double2 v = src[(long long)jx * stride];
-      double2 w = ph[q];
+      const cr v = slab[jx * DL_DFT_TILE + ss];
+      const cr w = phs[q];
       re += v.x * w.x - v.y * w.y;
       im += v.x * w.y + v.y * w.x;
       q += n;
       if (q >= len) q -= len;
     }
-    out[idx] = make_double2(re, im);
+    out[(b * nk + k) * stride + s0 + ss] = make_double2((double)re, (double)im);
   }
 }
 
@@ -330,6 +505,7 @@ __global__ void add_exact_kernel(LatDesc L, int np, int nd, int ip0, const doubl
   out[o].y += scale * ex[ab].y;
 }
 
+
 // acc[k] += sign * sum_col (blk[col][k] - sub[col][k])  (sub may be null)
 __global__ void col_accumulate_kernel(const double2* __restrict__ blk, const double2* __restrict__ sub, int ncol,
                                       long long per_col, double sign, double2* acc) {
@@ -428,16 +604,56 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
   return cudaErrorInvalidValue;
 }
 
+cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+                       FieldRef eta_o, const void* g64, int mx, double2* G1, cudaStream_t st) {
+  const LatDesc& L = B.lat[0];
+  const int npad = 1 << L.lognpad;
+  int cwlog = L.lognpad;
+  while (cwlog > 0 && (L.X << cwlog) > 256) --cwlog;  // X * cw <= 256 threads per CTA
+  const int threads = L.X << cwlog;
+  if (threads > 256 || threads < 1) return cudaErrorInvalidValue;
+  const dim3 grid(L.T * L.Z * L.Y, npad >> cwlog);
+  const double2* gg = (const double2*)g64;
+#define CX(PR, MD, R)                                                                                              \
+  if (prec == PR && mode == MD) {                                                                                  \
+    const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + L.X) * 2 * sizeof(R);                                   \
+    if (with_deriv) {                                                                                              \
+      cudaFuncSetAttribute(contract_x_kernel<PR, MD, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
+      DL_COUNT();                                                                                                  \
+      contract_x_kernel<PR, MD, true, R><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gg, mx, cwlog, G1); \
+    } else {                                                                                                       \
+      cudaFuncSetAttribute(contract_x_kernel<PR, MD, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
+      DL_COUNT();                                                                                                  \
+      contract_x_kernel<PR, MD, false, R><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gg, mx, cwlog, G1); \
+    }                                                                                                              \
+    return cudaGetLastError();                                                                                     \
+  }
+  CX(P64, 0, double) CX(P64, 1, double) CX(P64, 2, double) CX(P64, 3, double)
+  CX(P32, 0, float) CX(P32, 1, float) CX(P32, 2, float) CX(P32, 3, float)
+#undef CX
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
-                     cudaStream_t st) {
+                     int fp32, cudaStream_t st) {
   DL_COUNT();
   phase_kernel<<<(len + 63) / 64, 64, 0, st>>>(len, phase);
-  long long tot = nb * (2 * m + 1) * stride;
-  long long g = (tot + 255) / 256;
-  if (g > 152LL * 64) g = 152LL * 64;
-  if (g < 1) g = 1;
+  const long long ntile = (stride + DL_DFT_TILE - 1) / DL_DFT_TILE;
+  const long long g = nb * ntile;
+  if (g <= 0) return cudaSuccess;
+  if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
   DL_COUNT();
-  dft_kernel<<<(int)g, 256, 0, st>>>(in, out, nb, len, stride, m, phase);
+  if ((size_t)(len * DL_DFT_TILE + len) * 2 * (fp32 ? sizeof(float) : sizeof(double)) > 200000)
+    return cudaErrorInvalidValue;  // extents up to ~190 (FP64) / ~380 (FP32) sites
+  if (fp32) {
+    const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(float);
+    cudaFuncSetAttribute(dft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    dft_kernel<float><<<(int)g, 256, smem, st>>>(in, out, nb, len, stride, m, phase);
+  } else {
+    const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(double);
+    cudaFuncSetAttribute(dft_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    dft_kernel<double><<<(int)g, 256, smem, st>>>(in, out, nb, len, stride, m, phase);
+  }
   return cudaGetLastError();
 }
 
