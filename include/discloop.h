@@ -226,6 +226,29 @@ dl_status dl_profile(dl_ctx* ctx, int enable, double* out);
  * launches plus the kernel nodes of every CUDA-graph launch).  Thread-safe. */
 long long dl_kernel_launches(void);
 
+/* ---- allocation-free variant ----------------------------------------------- */
+
+/* dl_apply without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * moment they apply an operator, for example a host framework whose caching
+ * allocator already owns the device memory, or a latency-critical loop that
+ * must not wait on cudaMalloc's implicit synchronisation.  It computes exactly
+ * what dl_apply computes (same kernels, same arguments and layouts; the
+ * context's gauge field must be loaded), but its seven working fields come
+ * from one fixed device array of 64 MiB that the library holds on every GPU
+ * that loads it, until the process exits.  Sizes whose working fields exceed
+ * that array are rejected with DL_ERR_ARG and a message (the limit is
+ * 7 x ceil256(V/2 x npad x site bytes [+ 4-byte scales for DL_F16]) <= 64 MiB,
+ * npad = n rounded up to a power of two, site bytes 192 / 96 / 48 for
+ * DL_F64 / DL_F32 / DL_F16; e.g. 16^3 x 8 with n = 8 in FP64 fits).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  The array
+ * is shared by every call and keeps the previous call's contents (each call
+ * overwrites all of it that it reads), so calls that may overlap on the GPU,
+ * from any context or stream, race and must be serialised by the caller. */
+dl_status dl_apply_noalloc(dl_ctx* ctx, int op, int prec, int flavour, int n,
+                           const void* in, const void* aux, void* out, int dtype);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ _SIGS = {
                               C.c_void_p, C.c_int]),
     "dl_hpe_exact": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dl_kernel_launches": (C.c_longlong, []),
+    "dl_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_int]),
     "dl_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dl_tsm_run": (C.c_int, [C.c_void_p, C.POINTER(dl_tsm_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(dl_tsm_info)]),
@@ -205,3 +207,9 @@ def dl_profile(ctx, enable=-1):
 
 def dl_kernel_launches():
     return int(lib().dl_kernel_launches())
+
+
+def dl_apply_noalloc(ctx, op, prec, flavour, n, inp, aux, out, dtype=DL_C128):
+    """dl_apply with its working fields in the library's fixed 64 MiB device array (no allocation)."""
+    return _check(ctx, lib().dl_apply_noalloc(ctx, int(op), int(prec), int(flavour), int(n), _ptr(inp), _ptr(aux),
+                                              _ptr(out), int(dtype)))

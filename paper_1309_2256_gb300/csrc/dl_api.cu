@@ -17,6 +17,7 @@
 #include "dl_kernels.h"
 
 #include <atomic>
+#include <mutex>
 
 static std::atomic<long long> g_launches{0};
 void dl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -1287,3 +1288,129 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free operator application.
+//
+// Some callers cannot allocate device memory when they apply an operator: a
+// host framework whose caching allocator already owns all device memory, a
+// latency-critical loop that must not wait for cudaMalloc's implicit device
+// synchronisation, or code that runs after its memory budget is fixed.  For
+// them dl_apply_noalloc does what dl_apply does, but its working fields live in
+// one file-scope device array of DL_NOALLOC_BYTES instead of the context's
+// workspace.  The array exists on every GPU that loads this library, for the
+// lifetime of the process.
+#define DL_NOALLOC_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DL_NOALLOC_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (the first call on a device does this, so it should come before
+// any stream capture).  In host code the array's name is only a stand-in.
+cudaError_t noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux,
+                                      void* out, int dtype) {
+  dl_status s;
+  if ((s = check_ctx(c, true)) != DL_OK) return s;
+  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec < 0 || prec > 2 ||
+      (dtype != DL_C128 && dtype != DL_C64) || op < DL_OP_M || op > DL_OP_BH)
+    return fail(c, DL_ERR_ARG, "dl_apply_noalloc: bad argument");
+  if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");
+  // seven parity fields (in, out, aux for both parities, one temporary), each
+  // 256-byte aligned, must fit the fixed array
+  const size_t items = (size_t)c->Vh << ilog2ceil(n);
+  const size_t data_b = (items * chunk_bytes(prec) + 255) & ~(size_t)255;
+  const size_t norm_b = prec == P16 ? ((items * sizeof(float) + 255) & ~(size_t)255) : 0;
+  const size_t need = 7 * (data_b + norm_b);
+  if (need > DL_NOALLOC_BYTES) {
+    char msg[200];
+    snprintf(msg, sizeof(msg), "dl_apply_noalloc: %zu bytes of working fields exceed the %llu-byte fixed scratch", need,
+             (unsigned long long)DL_NOALLOC_BYTES);
+    return fail(c, DL_ERR_ARG, msg);
+  }
+  if ((s = enter(c)) != DL_OK) return s;
+  unsigned char* base = nullptr;
+  CK(noalloc_scratch(c->dev, &base));
+  FieldRef fr[7];
+  for (int k = 0; k < 7; ++k) {
+    unsigned char* p = base + (size_t)k * (data_b + norm_b);
+    fr[k] = FieldRef{p, prec == P16 ? (float*)(p + data_b) : nullptr};
+  }
+  const FieldRef ie = fr[0], io = fr[1], oe = fr[2], oo = fr[3], ae = fr[4], ao = fr[5], t = fr[6];
+  Batch B = make_batch(c, n);
+  CK(dl::pack(B, prec, 0, ie, in, dtype, c->st));
+  CK(dl::pack(B, prec, 1, io, in, dtype, c->st));
+  if (aux) {
+    CK(dl::pack(B, prec, 0, ae, aux, dtype, c->st));
+    CK(dl::pack(B, prec, 1, ao, aux, dtype, c->st));
+  }
+  GaugeSet g{c->g64, c->g32, c->g16};
+  const int gr = grec_of(c, prec);
+  auto D = [&](int epi_kind, bool dag, int par, FieldRef src, FieldRef ax, FieldRef dst, const EpiSet& E) {
+    return dl::dslash(B, prec, gr, epi_kind, dag, par, src, ax, dst, g, E, nullptr, nullptr, NOF, NOF, NOF, nullptr,
+                      c->st);
+  };
+  switch (op) {
+    case DL_OP_M:
+    case DL_OP_MDAG: {
+      const bool dag = op == DL_OP_MDAG;
+      EpiSet E = epi(c, -c->kappa, 0, 0, 1, dag ? -f : f);
+      CK(D(EPI_AUX, dag, 0, io, ie, oe, E));
+      CK(D(EPI_AUX, dag, 1, ie, io, oo, E));
+      break;
+    }
+    case DL_OP_HOP: {
+      EpiSet E = epi(c, 1.0, 0, 0, 0, 0);
+      CK(D(EPI_PLAIN, false, 0, io, NOF, oe, E));
+      CK(D(EPI_PLAIN, false, 1, ie, NOF, oo, E));
+      break;
+    }
+    case DL_OP_MHAT:
+    case DL_OP_MHAT_DAG: {
+      const bool dag = op == DL_OP_MHAT_DAG;
+      CK(stage1(c, B, prec, dag, f, ie, t, nullptr));
+      CK(stage2(c, B, prec, dag, f, t, ie, oe, nullptr, nullptr));
+      CK(dl::zero(B, prec, oo, nullptr, c->st));
+      break;
+    }
+    case DL_OP_PREP: {
+      EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+      CK(dl::twist(B, prec, t, io, Ei, nullptr, c->st));
+      EpiSet E = epi(c, c->kappa, 0, 0, 0, 0);
+      CK(D(EPI_AUX, false, 0, t, ie, oe, E));
+      CK(dl::zero(B, prec, oo, nullptr, c->st));
+      break;
+    }
+    case DL_OP_RECON: {
+      CK(dl::copy(B, prec, prec, oe, ie, nullptr, c->st));
+      EpiSet E = epi(c, c->kappa, 2, f, 0, 0);
+      CK(D(EPI_AUX, false, 1, ie, ao, oo, E));
+      break;
+    }
+    case DL_OP_BH: {
+      EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+      CK(D(EPI_PLAIN, false, 0, io, NOF, oe, E));
+      CK(D(EPI_PLAIN, false, 1, ie, NOF, oo, E));
+      break;
+    }
+  }
+  CK(dl::unpack(B, prec, 0, out, oe, dtype, c->st));
+  CK(dl::unpack(B, prec, 1, out, oo, dtype, c->st));
+  return leave(c);
+}
