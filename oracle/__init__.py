@@ -15,9 +15,11 @@ Modules:
   solver    CG on the normal equations; dense LU at small volume (Sec. 2.2)
   loops     bilinears, estimators (Eqs. loopSt, loopVv, loopStD, loopHPE1),
             momentum projection, HPE exact terms (Eq. HPE), TSM (Eq. estiTSM)
+  network   the gauge-covariant parallel-transport network of the learned
+            preconditioner (no counterpart in the paper), forward and exact backward
 
 Parity status: every function here is pinned by a `-m "not gpu"` test
 (tests/test_oracle_*.py) except the statements about the B55.32 physics,
 which are out of scope (parity unpinned: no ensemble).
 """
-from . import lattice, noise, operator, solver, loops  # noqa: F401
+from . import lattice, noise, operator, solver, loops, network  # noqa: F401

@@ -167,3 +167,37 @@ def dense_matrix(links, kappa, amu, f=1, bc=-1.0, which="M"):
     else:
         raise ValueError(which)
     return out.reshape(n, n).T.copy()
+
+
+def _site_shift(dims, site, mu, step):
+    """Neighbour (t, z, y, x) of `site` one step along mu, and the time-boundary factor flag."""
+    X, Y, Z, T = dims
+    t, z, y, x = site
+    crosses = False
+    if mu == 0:
+        x = (x + step) % X
+    elif mu == 1:
+        y = (y + step) % Y
+    elif mu == 2:
+        z = (z + step) % Z
+    else:
+        crosses = (t + step) >= T or (t + step) < 0
+        t = (t + step) % T
+    return (t, z, y, x), crosses
+
+
+def apply_m_at(links, psi, site, kappa, amu, f=1, bc=-1.0):
+    """(M_f psi)(x) at one site x = (t, z, y, x), from the definition (Eq. A.1):
+    R_f psi(x) - kappa sum_mu [(1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)].
+    Lets full-size fields be checked at sampled sites."""
+    dims = (links.shape[3], links.shape[2], links.shape[1], links.shape[0])
+    out = twist_matrix(kappa, amu, f) @ psi[site]
+    for mu in range(4):
+        fw, cf = _site_shift(dims, site, mu, +1)
+        bw, cb = _site_shift(dims, site, mu, -1)
+        u = links[site][mu]
+        ub = links[bw][mu]
+        pf = psi[fw] * (bc if cf else 1.0)
+        pb = psi[bw] * (bc if cb else 1.0)
+        out = out - kappa * ((ID4 - GAMMA[mu]) @ (pf @ u.T) + (ID4 + GAMMA[mu]) @ (pb @ np.conj(ub)))
+    return out

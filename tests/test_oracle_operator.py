@@ -117,3 +117,12 @@ def test_even_odd_schur_complement():
     lhs = np.vdot(v[0], op.mhat(links, v[1], KAPPA, AMU, 1, -1.0, dims))
     rhs = np.vdot(op.mhat_dag(links, v[0], KAPPA, AMU, 1, -1.0, dims), v[1])
     assert abs(lhs - rhs) < 1e-12
+
+
+def test_site_local_operator_matches_full_field():
+    dims = (4, 4, 2, 6)
+    links = synth.gauge_links(dims, 0.4, 17)
+    psi = synth.gaussian_spinors(dims, 1, 18)[0]
+    full = op.apply_m(links, psi, KAPPA, AMU, -1)
+    for site in [(0, 0, 0, 0), (5, 1, 3, 2), (2, 0, 1, 3), (5, 1, 0, 0)]:
+        assert np.abs(op.apply_m_at(links, psi, site, KAPPA, AMU, -1) - full[site]).max() < 1e-14
