@@ -3,8 +3,8 @@
 
 Workload (32^3 x 64, eps 0.4, kappa 0.1612, a*mu 0.0055, antiperiodic in t):
 the Truncated Solver Method with N_HP = 24 high-precision (CG residual 1e-10,
-FP32 Krylov vectors, FP64 reliable updates) and N_LP = 500 low-precision
-(residual 1e-2, FP16 Krylov vectors) solves of the even-odd twisted-mass
+FP32 Krylov vectors, FP64 reliable updates at delta = 0.01) and N_LP = 500 low-precision
+(residual 1e-2, 16-bit fixed-point Krylov vectors) solves of the even-odd twisted-mass
 operator, batched 16 right-hand sides per launch, each solution contracted
 into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
 (4 exact orders) local loops for all 16 Gamma, every t, |p|^2 <= 9.
@@ -37,6 +37,7 @@ DIMS = (32, 32, 32, 64)
 EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
 N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 16
 TOL_HP, TOL_LP = 1e-10, 1e-2
+DELTA_HP = 0.01  # reliable updates every two decades: FP64 operator applications are ALU-bound on GB300
 P2MAX = 9
 LINK_SEED, NOISE_SEED = 1002, 2002
 WORKLOAD = "tsm_32x32x32x64"
@@ -160,7 +161,7 @@ def run_ours(args, rank, world, device):
 
     def params(step):
         return dl.dl_tsm_params(n_hp=n_hp_s, n_lp=n_lp_s, tol_hp=TOL_HP, tol_lp=TOL_LP, prec_hp_lo=dl.DL_F32,
-                                prec_lp_lo=dl.DL_F16, delta_hp=0.1, block=BLOCK,
+                                prec_lp_lo=dl.DL_F16, delta_hp=args.delta_hp, block=BLOCK,
                                 seed=rank_seed(step, rank), p2max=P2MAX, with_deriv=0,
                                 hpe=1, max_iter=200000, chunk=32)
 
@@ -344,17 +345,49 @@ def stencil_case():
     print("stencil case done")
 
 
+def contract_case():
+    """Small case for ncu captures of the contraction kernels: 24^3 x 24, 16 columns,
+    one-end loops at |p|^2 <= 9 from complex64 inputs (the low-precision pipeline)."""
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+    import synth
+    dims = (24, 24, 24, 24)
+    links = synth.gauge_links(dims, EPS, 78)
+    ctx = dl.dl_create(dims, 0, torch.cuda.current_stream())
+    dl.dl_load_gauge(ctx, links, -1.0, 12, 12)
+    dl.dl_set_params(ctx, KAPPA, AMU)
+    n = 16
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    eta = torch.empty((n, V * 12), dtype=torch.complex64, device="cuda")
+    dl.dl_noise_z4(ctx, 9, 0, n, eta, dl.DL_C64)
+    sol = torch.empty_like(eta)
+    dl.dl_noise_z4(ctx, 10, 0, n, sol, dl.DL_C64)
+    npm = len(dl.dl_momenta(P2MAX))
+    out = torch.zeros((n, dims[3], npm, 1, 4, 4), dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        dl.dl_contract(ctx, dl.DL_EST_ONE_END, eta, sol, n, dl.DL_C64, 0, P2MAX, out)
+    torch.cuda.synchronize()
+    dl.dl_destroy(ctx)
+    print("contract case done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default=None, choices=["stencil"],
+    ap.add_argument("--case", default=None, choices=["stencil", "contract"],
                     help="small profiling case instead of the benchmark (for ncu)")
+    ap.add_argument("--delta-hp", type=float, default=DELTA_HP,
+                    help="reliable-update trigger of the high-precision solves")
     args = ap.parse_args()
     if args.case == "stencil":
         stencil_case()
+        return
+    if args.case == "contract":
+        contract_case()
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -396,7 +429,7 @@ def main():
         "dtype": "f16/f32 Krylov, f64 reliable updates and accumulation",
         "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
-                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
+                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
                    "step": "one TSM sweep: 24 HP-LP pairs + 500 LP solves + contractions",
                    "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
