@@ -140,6 +140,18 @@ def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def _nvtx(torch, name):
+    """Push (name) or pop (None) an NVTX range around the timed steps, so that a
+    profiler can restrict its launch list to them; a no-op where NVTX is absent."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def _links():
     import synth
     return synth.gauge_links(DIMS, EPS, LINK_SEED)
@@ -190,6 +202,7 @@ def run_ours(args, rank, world, device):
     launches0 = dl.dl_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(device) as clk:
+        _nvtx(torch, "dl_timed")
         ev0.record(stream)
         t0 = time.perf_counter()
         for i in range(args.steps):
@@ -197,6 +210,7 @@ def run_ours(args, rank, world, device):
         ev1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        _nvtx(torch, None)
     if dist:
         tdist.barrier()
     launches = dl.dl_kernel_launches() - launches0
@@ -372,17 +386,175 @@ def contract_case():
     print("contract case done")
 
 
+def learned_case(args):
+    """The learned preconditioner on 16^3 x 32 (eps 0.4, kappa 0.161, a*mu 0.0055): a
+    4-layer, 16-channel network (FP32 weights, bfloat16 activations) trained with Adam
+    on (Z4 noise, FP64-accurate solution) pairs from the plain solver, then on fresh
+    noise: flexible GCR to 1e-10 with and without it against the mixed-precision CG,
+    and the TSM with the network as its LP map against truncated CG."""
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+    import synth
+    cfg = synth.CONFIGS["learned_16x16x16x32"]
+    dims, kappa, amu = cfg["dims"], cfg["kappa"], cfg["amu"]
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    links = synth.gauge_links(dims, cfg["eps"], 1000 + cfg["id"])
+    ctx = dl.dl_create(dims, 0, torch.cuda.current_stream())
+    dl.dl_load_gauge(ctx, links, -1.0, 12, 8)
+    dl.dl_set_params(ctx, kappa, amu)
+    out = {"case": "learned_16x16x16x32", "data": "synthetic", "pairs": args.pairs, "fresh": args.fresh}
+    # training pairs from the plain solver (complex64 storage, FP64-accurate solutions)
+    eta = torch.empty((args.pairs, V * 12), dtype=torch.complex64, device="cuda")
+    sol = torch.empty_like(eta)
+    hp = dl.dl_solve_params(tol=1e-10, max_iter=100000, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.01, flavour=1,
+                            chunk=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(0, args.pairs, 32):
+        n = min(32, args.pairs - b)
+        dl.dl_noise_z4(ctx, 2000 + cfg["id"], b, n, eta[b:b + n], dl.DL_C64)
+        dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
+    torch.cuda.synchronize()
+    out["seconds_pairs"] = time.perf_counter() - t0
+    nn = dl.dl_nn_create(ctx, 4, 16, dl.DL_BF16)
+    dl.dl_nn_set_weights(nn, synth.network_weights(4, 16, 3000 + cfg["id"]))
+    tp = dl.dl_nn_train_params(steps=args.train_steps, batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
+                               seed=11)
+    t0 = time.perf_counter()
+    hist = dl.dl_nn_train(nn, tp, args.pairs, eta, sol, dl.DL_C64)
+    torch.cuda.synchronize()
+    ttrain = time.perf_counter() - t0
+    k = max(1, min(20, len(hist) // 5))
+    out["train"] = {"steps": args.train_steps, "batch": args.batch, "lr": args.lr, "seconds": ttrain,
+                    "pair_passes_per_s": args.train_steps * args.batch / ttrain,
+                    "loss_first": float(hist[:k].mean()), "loss_last": float(hist[-k:].mean())}
+    # inference: one network application, timed with events on the current stream
+    one_in = eta[:1].clone()
+    one_out = torch.empty_like(one_in)
+    for _ in range(3):
+        dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_apply = e0.elapsed_time(e1) / reps
+    # flops of one application, per site and layer: channel mixing, 9 terms x 12 components x 2
+    # complex multiply-adds (8 flops each) per (output, input) channel pair; transports, 8 links x
+    # 4 spins x 9 complex multiply-adds per input channel
+    flops = 0
+    for l in range(4):
+        ci = 1 if l == 0 else 16
+        co = 1 if l == 3 else 16
+        flops += V * (co * ci * 9 * 12 * 2 * 8 + ci * 8 * 4 * 3 * 3 * 8)
+    out["apply"] = {"ms": ms_apply, "tflops": flops / ms_apply / 1e9, "flops_per_apply": flops}
+    # fresh noise: FGCR with / without the network, plain mixed-precision CG
+    fresh = torch.empty((args.fresh, V * 12), dtype=torch.complex128, device="cuda")
+    for b in range(0, args.fresh, 32):
+        n = min(32, args.fresh - b)
+        dl.dl_noise_z4(ctx, 5000 + cfg["id"], b, n, fresh[b:b + n])
+    fg = dl.dl_fgcr_params(tol=1e-10, max_iter=5000, restart=16, inner_tol=1e-4, flavour=1)
+    n_fg = min(args.fresh, args.fgcr_rhs)
+    for name, net in (("fgcr_net", nn), ("fgcr_plain", None)):
+        x = torch.empty((n_fg, V * 12), dtype=torch.complex128, device="cuda")
+        its, secs, ops, nns, res = [], 0.0, 0, 0, []
+        for b in range(0, n_fg, 8):
+            n = min(8, n_fg - b)
+            st, stt = dl.dl_fgcr_solve(ctx, net, fg, n, fresh[b:b + n], x[b:b + n])
+            its += list(stt.iters[:n])
+            res += list(stt.true_resid[:n])
+            secs += stt.seconds
+            ops += stt.op_applications
+            nns += stt.nn_applications
+        out[name] = {"rhs": n_fg, "iters_mean": float(np.mean(its)), "true_resid_max": float(np.max(res)),
+                     "seconds_per_rhs": secs / n_fg, "op_applications_per_rhs": ops / n_fg,
+                     "nn_applications_per_rhs": nns / n_fg}
+    x = torch.empty_like(fresh)
+    its, secs = [], 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(0, args.fresh, 16):
+        n = min(16, args.fresh - b)
+        stt = dl.dl_solve_stats()
+        dl.dl_solve(ctx, fresh[b:b + n], x[b:b + n], n, dl.DL_C128, hp, stt)
+        its += list(stt.iters[:n])
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    out["cg_plain"] = {"rhs": args.fresh, "iters_mean": float(np.mean(its)), "seconds_per_rhs": secs / args.fresh,
+                       "op_applications_per_rhs": 2.0 * float(np.mean(its)),
+                       "how": "even-odd CGNR, FP32 Krylov vectors, FP64 reliable updates, blocks of 16"}
+    # TSM: the network as LP map against truncated CG, same HP set
+    npm = len(dl.dl_momenta(0))
+    for name, net in (("tsm_net_lp", nn), ("tsm_cg_lp", None)):
+        prm = dl.dl_tsm_params(n_hp=24, n_lp=args.fresh, tol_hp=1e-10, tol_lp=1e-2, prec_hp_lo=dl.DL_F32,
+                               prec_lp_lo=dl.DL_F16, delta_hp=0.01, block=16, seed=7000 + cfg["id"], p2max=0,
+                               with_deriv=0, hpe=0, max_iter=100000, chunk=32, lp_net=nn["h"] if net else None)
+        loops_ = np.zeros((2, dims[3], npm, 1, 4, 4), dtype=np.complex128)
+        ohp, opr, olp = np.zeros((24, 4)), np.zeros((24, 4)), np.zeros((args.fresh, 4))
+        st, info = dl.dl_tsm_run(ctx, prm, loops_, ohp, opr, olp)
+        ee = _equal_error(ohp, opr, olp, 24, args.fresh, info.seconds_total)
+        out[name] = {"seconds": info.seconds_total, "seconds_lp": info.seconds_lp,
+                     "sigma_per_s": ee["sigma"]["per_s"], "axial_per_s": ee["axial"]["per_s"],
+                     "r_c_sigma": ee["sigma"]["r_c"], "r_c_axial": ee["axial"]["r_c"]}
+    dl.dl_nn_destroy(nn)
+    dl.dl_destroy(ctx)
+    print(json.dumps(out))
+
+
+def batch_case(args):
+    """Six lattices (two each of 12^3 x 24, 16^3 x 32, 24^3 x 48; eps 0.4, kappa 0.161,
+    a*mu 0.0055), 32 Z4 noise vectors each, solved together to 1e-8 (FP32 Krylov, FP64
+    reliable updates, autotuned right-hand-side tile) with zero-momentum loops."""
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+    import synth
+    dims = [(12, 12, 12, 24)] * 2 + [(16, 16, 16, 32)] * 2 + [(24, 24, 24, 48)] * 2
+    n = 32
+    ctx = dl.dl_create_multi(dims, 0, torch.cuda.current_stream())
+    for i, d in enumerate(dims):
+        dl.dl_load_gauge_lat(ctx, i, synth.gauge_links(d, 0.4, 1004 + 10 * i), -1.0, 12, 12)
+    dl.dl_set_params(ctx, 0.161, 0.0055)
+    out = np.zeros(sum(2 * n * d[3] * 16 for d in dims), dtype=np.complex128)
+    res = {"case": "batch_6_lattices", "data": "synthetic", "rhs_per_lattice": n}
+    for rep in range(2):
+        prm = dl.dl_batch_params(n=n, tol=1e-8, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.1, seed=2004 + rep,
+                                 max_iter=20000, tile=0)
+        st, info = dl.dl_batch_loops(ctx, prm, out, None)
+    res.update({"tile": info.tile, "instances": info.instances, "seconds_tune": info.seconds_tune,
+                "seconds_solve": info.seconds_solve, "seconds_contract": info.seconds_contract,
+                "iters_max": list(info.iters_max[:6]), "resid_max": list(info.resid_max[:6]),
+                "solves_per_s": 6 * n / (info.seconds_solve + info.seconds_contract)})
+    dl.dl_destroy(ctx)
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default=None, choices=["stencil", "contract"],
+    ap.add_argument("--case", default=None, choices=["stencil", "contract", "learned", "batch"],
                     help="small profiling case instead of the benchmark (for ncu)")
     ap.add_argument("--delta-hp", type=float, default=DELTA_HP,
                     help="reliable-update trigger of the high-precision solves")
+    ap.add_argument("--pairs", type=int, default=2000, help="learned case: training pairs")
+    ap.add_argument("--fresh", type=int, default=200, help="learned case: fresh noise vectors")
+    ap.add_argument("--fgcr-rhs", type=int, default=200, help="learned case: fresh vectors solved by FGCR")
+    ap.add_argument("--train-steps", type=int, default=1000, help="learned case: Adam steps")
+    ap.add_argument("--batch", type=int, default=4, help="learned case: pairs per Adam step")
+    ap.add_argument("--lr", type=float, default=1e-3, help="learned case: Adam learning rate")
     args = ap.parse_args()
+    if args.case == "learned":
+        learned_case(args)
+        return
+    if args.case == "batch":
+        batch_case(args)
+        return
     if args.case == "stencil":
         stencil_case()
         return

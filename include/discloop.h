@@ -43,6 +43,7 @@ extern "C" {
 #endif
 
 typedef struct dl_ctx dl_ctx;
+typedef struct dl_nn dl_nn;   /* learned preconditioner (see the section at the end) */
 
 typedef enum {
   DL_OK = 0,
@@ -189,6 +190,10 @@ typedef struct {
   int hpe;               /* add the HPE standard-estimator loops */
   int max_iter;
   int chunk;
+  dl_nn* lp_net;         /* NULL: LP solutions by truncated CG.  Otherwise the learned
+                            map's output N(eta) stands in for every LP solution (on the
+                            context's first-flavour operator); the HP correction of
+                            Eq. estiTSM keeps the estimate unbiased for any map. */
 } dl_tsm_params;
 
 typedef struct {
@@ -208,6 +213,52 @@ typedef struct {
  *          zero momentum, summed over t) for error estimates. */
 dl_status dl_tsm_run(dl_ctx* ctx, const dl_tsm_params* params, double* loops,
                      double* obs_hp, double* obs_lp_pair, double* obs_lp, dl_tsm_info* info);
+
+/* ---- several lattices in one batch ------------------------------------------ */
+
+/* A context over nlat independent lattices (dims: int[nlat][4]), e.g. several
+ * gauge configurations or ensembles, whose solves share every kernel launch.
+ * Only dl_load_gauge_lat, dl_set_params_lat, dl_set_params (all lattices) and
+ * dl_batch_loops accept a multi-lattice context; nlat <= 16. */
+dl_status dl_create_multi(dl_ctx** ctx, int nlat, const int* dims, int device, void* cuda_stream);
+/* dl_load_gauge for lattice `lat` (every lattice must use the same recon choice). */
+dl_status dl_load_gauge_lat(dl_ctx* ctx, int lat, const double* links, int links_on_device,
+                            double t_boundary, int recon_f32, int recon_f16);
+/* kappa and a*mu of lattice `lat` (Eq. A.1). */
+dl_status dl_set_params_lat(dl_ctx* ctx, int lat, double kappa, double amu);
+
+typedef struct {
+  int n;            /* noise vectors per lattice; n * nlat <= 256 */
+  double tol;       /* CG residual bound (Sec. 2.2), as in dl_solve_params */
+  int prec_hi;      /* DL_F64 or DL_F32 */
+  int prec_lo;      /* Krylov storage, DL_F64 / DL_F32 / DL_F16 */
+  double delta;     /* reliable-update trigger, 0 = never */
+  uint64_t seed;    /* noise r of lattice l is index l * n + r of the dl_noise_z4 stream */
+  int max_iter;
+  int tile;         /* right-hand sides per instance: 4, 8, 16 or 32; 0 = fastest of 8/16/32
+                       from a short timed run (autotuning) */
+} dl_batch_params;
+
+typedef struct {
+  int tile, instances;
+  double seconds_tune, seconds_solve, seconds_contract;
+  int iters_max[16];     /* per lattice */
+  double resid_max[16];  /* per lattice, CG residual |r|/|Mhat^dag bhat| */
+  int not_converged;
+} dl_batch_info;
+
+/* Z4 noise, even-odd solve (flavour u) and local loops at zero momentum for n
+ * noise vectors on every lattice of a multi-lattice context.  Every lattice's
+ * n right-hand sides are split into instances of `tile` columns that share its
+ * gauge field; one CUDA-graph loop (conditional WHILE node) iterates CG over all
+ * instances of all lattices at once, each column masked out when it converges.
+ * loops (host, complex128, may be NULL): per lattice in order,
+ *   [2][n][T_l][4][4]: one-end (Eq. loopVv, factor -4i kappa amu) then
+ *   generalised one-end (Eq. loopStD, factor 2), summed over space per t.
+ * sol (device, complex128, may be NULL): per lattice in order, natural fields
+ *   [n][T_l][Z_l][Y_l][X_l][4][3]. */
+dl_status dl_batch_loops(dl_ctx* ctx, const dl_batch_params* params, double* loops, void* sol,
+                         dl_batch_info* info);
 
 /* ---- instrumentation ------------------------------------------------------ */
 
@@ -248,6 +299,75 @@ long long dl_kernel_launches(void);
  * from any context or stream, race and must be serialised by the caller. */
 dl_status dl_apply_noalloc(dl_ctx* ctx, int op, int prec, int flavour, int n,
                            const void* in, const void* aux, void* out, int dtype);
+
+/* ---- learned preconditioner (no counterpart in the paper) ------------------- */
+
+/* A gauge-covariant network N of parallel-transport convolution layers on the
+ * context's lattice and gauge field.  Layer l maps C_in channel fields x_i to
+ * C_out fields
+ *   y_o(x) = sum_i [ sum_b W[0][b][o][i] L_b x_i(x)
+ *                  + sum_mu sum_b W[1+2mu][b][o][i] H_b(mu) U_mu(x) x_i(x+mu)
+ *                  + sum_mu sum_b W[2+2mu][b][o][i] H_b(mu) U_mu(x-mu)^+ x_i(x-mu) ]
+ * with L_b in {1, g5} (b < 2; W[0][2..3] unused, keep them zero) and
+ * H_b(mu) in {1, g_mu, g5, g5 g_mu}; hops across t = T-1 <-> 0 carry the
+ * context's time-boundary factor.  Weights act on channels and spin only, so
+ * N commutes with gauge transformations.  Channels run 1 -> C -> ... -> C -> 1.
+ * Weights are complex64, per layer [9][4][C_out][C_in], layers concatenated;
+ * activations are stored in FP32 (act_prec = DL_F32) or bfloat16 (act_prec =
+ * 3), arithmetic is FP32.  The network uses the FP32 gauge copy (its recon). */
+#define DL_BF16 3
+dl_status dl_nn_create(dl_ctx* ctx, int n_layers, int channels, int act_prec, dl_nn** out);
+void dl_nn_destroy(dl_nn* nn);
+/* Complex weights over all layers (the length of the set/get arrays / 2 floats). */
+long long dl_nn_weight_count(const dl_nn* nn);
+dl_status dl_nn_set_weights(dl_nn* nn, const float* host_w);   /* host complex64 */
+dl_status dl_nn_get_weights(dl_nn* nn, float* host_w);
+/* out_k = N(in_k) for n natural full-lattice fields (device, dtype). */
+dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype);
+/* Loss sum_k |N(eta_k) - s_k|^2 / |s_k|^2 over n pairs (device natural fields)
+ * and its gradient with respect to conj(W) times 2 (host complex64, weight
+ * layout); either output may be NULL. */
+dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int dtype, double* loss,
+                          float* grad);
+
+typedef struct {
+  int steps;            /* Adam steps */
+  int batch;            /* pairs per step (mean loss) */
+  double lr, beta1, beta2, eps;
+  uint64_t seed;        /* order of the pairs: a seeded shuffle per pass */
+} dl_nn_train_params;
+
+/* Adam on the mean loss over minibatches of the n_pairs (eta, s) pairs (device
+ * natural fields, dtype).  loss_hist (host, may be NULL) receives the mean
+ * minibatch loss of every step. */
+dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* params, int n_pairs, const void* eta,
+                      const void* s, int dtype, double* loss_hist);
+
+/* Flexible GCR (Eisenstat, Elman & Schultz 1983; flexible preconditioning as
+ * in Saad 1993) on the full operator M_f, right-preconditioned by the network
+ * (or by the identity when nn is NULL): FP32 inner cycles of at most `restart`
+ * directions, each started from the FP64 true residual b - M x and stopped at
+ * inner_tol relative to it; the FP64 solution is updated after every cycle
+ * until ||b - M x|| <= tol ||b||. */
+typedef struct {
+  double tol;        /* true relative residual bound */
+  int max_iter;      /* inner iterations per right-hand side */
+  int restart;       /* directions per inner cycle, 1..32 */
+  double inner_tol;  /* relative residual reduction per inner cycle */
+  int flavour;       /* +1 (u) or -1 (d) */
+} dl_fgcr_params;
+
+typedef struct {
+  int iters[DL_MAX_RHS];        /* inner iterations */
+  int cycles[DL_MAX_RHS];       /* inner cycles (FP64 residual recomputations) */
+  double true_resid[DL_MAX_RHS];
+  long long op_applications;    /* M applications, FP32 and FP64 */
+  long long nn_applications;
+  double seconds;
+} dl_fgcr_stats;
+
+dl_status dl_fgcr_solve(dl_ctx* ctx, dl_nn* precond, const dl_fgcr_params* params, int n,
+                        const void* src, void* sol, int dtype, dl_fgcr_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdiscloop.so")
 
 DL_OK, DL_ERR_ARG, DL_ERR_CUDA, DL_ERR_OOM, DL_ERR_STATE = 0, -1, -2, -3, -4
 DL_NOT_CONVERGED, DL_BREAKDOWN = 1, 3
-DL_F64, DL_F32, DL_F16 = 0, 1, 2
+DL_F64, DL_F32, DL_F16, DL_BF16 = 0, 1, 2, 3
 DL_C128, DL_C64 = 0, 1
 (DL_OP_M, DL_OP_MDAG, DL_OP_HOP, DL_OP_MHAT, DL_OP_MHAT_DAG, DL_OP_PREP, DL_OP_RECON, DL_OP_BH) = range(8)
 DL_EST_STANDARD, DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE = range(4)
@@ -42,13 +42,40 @@ class dl_tsm_params(C.Structure):
     _fields_ = [("n_hp", C.c_int), ("n_lp", C.c_int), ("tol_hp", C.c_double), ("tol_lp", C.c_double),
                 ("prec_hp_lo", C.c_int), ("prec_lp_lo", C.c_int), ("delta_hp", C.c_double), ("block", C.c_int),
                 ("seed", C.c_uint64), ("p2max", C.c_int), ("with_deriv", C.c_int), ("hpe", C.c_int),
-                ("max_iter", C.c_int), ("chunk", C.c_int)]
+                ("max_iter", C.c_int), ("chunk", C.c_int), ("lp_net", C.c_void_p)]
 
 
 class dl_tsm_info(C.Structure):
     _fields_ = [("np", C.c_int), ("nd", C.c_int), ("n_est", C.c_int), ("seconds_total", C.c_double),
                 ("seconds_hp", C.c_double), ("seconds_lp", C.c_double), ("seconds_contract", C.c_double),
                 ("iters_hp", C.c_longlong), ("iters_lp", C.c_longlong), ("not_converged", C.c_int)]
+
+
+class dl_batch_params(C.Structure):
+    _fields_ = [("n", C.c_int), ("tol", C.c_double), ("prec_hi", C.c_int), ("prec_lo", C.c_int),
+                ("delta", C.c_double), ("seed", C.c_uint64), ("max_iter", C.c_int), ("tile", C.c_int)]
+
+
+class dl_batch_info(C.Structure):
+    _fields_ = [("tile", C.c_int), ("instances", C.c_int), ("seconds_tune", C.c_double),
+                ("seconds_solve", C.c_double), ("seconds_contract", C.c_double), ("iters_max", C.c_int * 16),
+                ("resid_max", C.c_double * 16), ("not_converged", C.c_int)]
+
+
+class dl_nn_train_params(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
+
+
+class dl_fgcr_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("restart", C.c_int), ("inner_tol", C.c_double),
+                ("flavour", C.c_int)]
+
+
+class dl_fgcr_stats(C.Structure):
+    _fields_ = [("iters", C.c_int * DL_MAX_RHS), ("cycles", C.c_int * DL_MAX_RHS),
+                ("true_resid", C.c_double * DL_MAX_RHS), ("op_applications", C.c_longlong),
+                ("nn_applications", C.c_longlong), ("seconds", C.c_double)]
 
 
 _lib = None
@@ -72,9 +99,25 @@ _SIGS = {
     "dl_kernel_launches": (C.c_longlong, []),
     "dl_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int]),
+    "dl_create_multi": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+    "dl_load_gauge_lat": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]),
+    "dl_set_params_lat": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double]),
+    "dl_batch_loops": (C.c_int, [C.c_void_p, C.POINTER(dl_batch_params), C.c_void_p, C.c_void_p,
+                                 C.POINTER(dl_batch_info)]),
     "dl_profile": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dl_tsm_run": (C.c_int, [C.c_void_p, C.POINTER(dl_tsm_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.POINTER(dl_tsm_info)]),
+    "dl_nn_create": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "dl_nn_destroy": (None, [C.c_void_p]),
+    "dl_nn_weight_count": (C.c_longlong, [C.c_void_p]),
+    "dl_nn_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dl_nn_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dl_nn_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "dl_nn_loss_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dl_nn_train": (C.c_int, [C.c_void_p, C.POINTER(dl_nn_train_params), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                              C.c_void_p]),
+    "dl_fgcr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(dl_fgcr_params), C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_int, C.POINTER(dl_fgcr_stats)]),
 }
 
 
@@ -213,3 +256,86 @@ def dl_apply_noalloc(ctx, op, prec, flavour, n, inp, aux, out, dtype=DL_C128):
     """dl_apply with its working fields in the library's fixed 64 MiB device array (no allocation)."""
     return _check(ctx, lib().dl_apply_noalloc(ctx, int(op), int(prec), int(flavour), int(n), _ptr(inp), _ptr(aux),
                                               _ptr(out), int(dtype)))
+
+
+def dl_create_multi(dims_list, device=0, stream=None):
+    h = C.c_void_p()
+    flat = [int(v) for d in dims_list for v in d]
+    arr = (C.c_int * len(flat))(*flat)
+    st = lib().dl_create_multi(C.byref(h), len(dims_list), arr, int(device), _stream_ptr(stream))
+    if st < 0:
+        raise DLError(st, "dl_create_multi failed")
+    return h.value
+
+
+def dl_load_gauge_lat(ctx, lat, links, t_boundary=-1.0, recon_f32=12, recon_f16=12):
+    on_dev = 0 if isinstance(links, np.ndarray) else 1
+    if on_dev == 0:
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+    return _check(ctx, lib().dl_load_gauge_lat(ctx, int(lat), _ptr(links), on_dev, float(t_boundary), int(recon_f32),
+                                               int(recon_f16)))
+
+
+def dl_set_params_lat(ctx, lat, kappa, amu):
+    return _check(ctx, lib().dl_set_params_lat(ctx, int(lat), float(kappa), float(amu)))
+
+
+def dl_batch_loops(ctx, params: dl_batch_params, loops=None, sol=None):
+    info = dl_batch_info()
+    st = _check(ctx, lib().dl_batch_loops(ctx, C.byref(params), _ptr(loops), _ptr(sol), C.byref(info)))
+    return st, info
+
+
+# ---- learned preconditioner ---------------------------------------------------
+# A network handle keeps its context for error messages: {"h": address, "ctx": ctx}.
+
+def dl_nn_create(ctx, n_layers, channels, act_prec=DL_BF16):
+    h = C.c_void_p()
+    _check(ctx, lib().dl_nn_create(ctx, int(n_layers), int(channels), int(act_prec), C.byref(h)))
+    return {"h": h.value, "ctx": ctx}
+
+
+def dl_nn_destroy(nn):
+    lib().dl_nn_destroy(nn["h"])
+
+
+def dl_nn_weight_count(nn):
+    return int(lib().dl_nn_weight_count(nn["h"]))
+
+
+def dl_nn_set_weights(nn, w):
+    w = np.ascontiguousarray(w, dtype=np.complex64)
+    assert w.size == dl_nn_weight_count(nn)
+    return _check(nn["ctx"], lib().dl_nn_set_weights(nn["h"], w.ctypes.data))
+
+
+def dl_nn_get_weights(nn):
+    w = np.zeros(dl_nn_weight_count(nn), dtype=np.complex64)
+    _check(nn["ctx"], lib().dl_nn_get_weights(nn["h"], w.ctypes.data))
+    return w
+
+
+def dl_nn_apply(nn, n, inp, out, dtype=DL_C128):
+    return _check(nn["ctx"], lib().dl_nn_apply(nn["h"], int(n), _ptr(inp), _ptr(out), int(dtype)))
+
+
+def dl_nn_loss_grad(nn, n, eta, s, dtype=DL_C128):
+    loss = np.zeros(1, dtype=np.float64)
+    grad = np.zeros(dl_nn_weight_count(nn), dtype=np.complex64)
+    _check(nn["ctx"], lib().dl_nn_loss_grad(nn["h"], int(n), _ptr(eta), _ptr(s), int(dtype), loss.ctypes.data,
+                                            grad.ctypes.data))
+    return float(loss[0]), grad
+
+
+def dl_nn_train(nn, params: dl_nn_train_params, n_pairs, eta, s, dtype=DL_C128):
+    hist = np.zeros(max(params.steps, 1), dtype=np.float64)
+    _check(nn["ctx"], lib().dl_nn_train(nn["h"], C.byref(params), int(n_pairs), _ptr(eta), _ptr(s), int(dtype),
+                                        hist.ctypes.data))
+    return hist[:params.steps]
+
+
+def dl_fgcr_solve(ctx, nn, params: dl_fgcr_params, n, src, sol, dtype=DL_C128):
+    stats = dl_fgcr_stats()
+    st = _check(ctx, lib().dl_fgcr_solve(ctx, nn["h"] if nn else None, C.byref(params), int(n), _ptr(src), _ptr(sol),
+                                         int(dtype), C.byref(stats)))
+    return st, stats

@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "discloop.h"
-#include "dl_kernels.h"
+#include "dl_host.h"
 
 #include <atomic>
 #include <mutex>
@@ -22,75 +22,8 @@
 static std::atomic<long long> g_launches{0};
 void dl_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-namespace {
 
-struct Field {
-  int prec = -1;
-  size_t items = 0;
-  void* data = nullptr;
-  float* norm = nullptr;
-  FieldRef ref() const { return FieldRef{data, norm}; }
-};
-
-struct GraphEntry {
-  std::string key;
-  cudaGraphExec_t exec = nullptr;
-  long long kernels = 0;  // kernel nodes in the graph
-};
-
-int ilog2ceil(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
-}
-
-size_t chunk_bytes(int prec) { return prec == P64 ? 192 : (prec == P32 ? 96 : 48); }
-
-}  // namespace
-
-struct dl_ctx {
-  int dev = 0;
-  cudaStream_t st = nullptr;    // internal stream (non-blocking; capturable)
-  cudaStream_t user = nullptr;  // caller's stream
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  int dims[4] = {0, 0, 0, 0};
-  int Vh = 0;
-  double kappa = 0.125, amu = 0.0, tbc = -1.0;
-  int rec32 = 12, rec16 = 8;
-  void* g64 = nullptr;
-  void* g32 = nullptr;
-  void* g16 = nullptr;
-  bool has_gauge = false;
-  std::string err;
-  std::map<std::string, Field> ws;
-  double* partial = nullptr;
-  size_t partial_blocks = 0;
-  int* loopctr = nullptr;  // iterations run by the current graph launch, and its limit
-  int* waitc = nullptr;    // per column: iterations spent waiting for a reliable update
-  double* S = nullptr;  // [DL_NS][DL_NCMAX]
-  int* active = nullptr;
-  int* flags = nullptr;
-  int* iters = nullptr;
-  int* upd = nullptr;
-  int* all = nullptr;  // all-ones mask
-  double2* misc = nullptr;  // small complex scratch (HPE exact part, observables)
-  int* mom = nullptr;
-  int mom_p2 = -1, np = 0;
-  void* scratch = nullptr;  // contraction scratch
-  size_t scratch_bytes = 0;
-  std::map<std::string, DevBuf> bufs;
-  std::vector<GraphEntry> graphs;
-  // live stencil timing: events around the four operator launches of the first
-  // CG iteration of every captured chunk; sums per (stage, precision)
-  int profiling = 0;
-  int prof_pending[3] = {0, 0, 0};  // take one stencil sample per precision when set
-  cudaEvent_t pev[8] = {nullptr};
-  double prof_ms[4][3] = {{0}};
-  long long prof_n[4][3] = {{0}};
-  long long prof_items[4][3] = {{0}};  // site-column items processed, summed over sampled launches
-};
-
-namespace {
+namespace dlh {
 
 dl_status fail(dl_ctx* c, dl_status s, const std::string& m) {
   if (c) c->err = m;
@@ -103,11 +36,6 @@ dl_status cuda_fail(dl_ctx* c, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
 }
 
-#define CK(expr)                                                   \
-  do {                                                             \
-    cudaError_t _e = (expr);                                       \
-    if (_e != cudaSuccess) return cuda_fail(c, _e, #expr);         \
-  } while (0)
 
 Batch make_batch(const dl_ctx* c, int ncol) {
   Batch B;
@@ -124,17 +52,55 @@ Batch make_batch(const dl_ctx* c, int ncol) {
   L.rhs_base = 0;
   L.item_off = 0;
   L.gsite_off = 0;
-  L.tbc = c->tbc;
-  L.kappa = c->kappa;
-  L.amu = c->amu;
+  L.tbc = c->lats[0].tbc;
+  L.kappa = c->lats[0].kappa;
+  L.amu = c->lats[0].amu;
+  L.noise_base = 0;
   B.pstride = (int)c->partial_blocks;
   dl::blocks_for(B, 256);
   return B;
 }
 
-// Twist T = a + i b gamma_5 for R_f (inv = false) or R_f^{-1} (inv = true).
-void twist_ab(const dl_ctx* c, int f, bool inv, double& a, double& b) {
-  double w = 2.0 * c->kappa * c->amu * f;
+// Batch over every lattice of the context: each lattice's n columns are split
+// into instances of `tile` columns (the last one ragged) sharing its gauge field;
+// instance k of lattice l draws noise indices l * n + k * tile + column.
+bool make_batch_multi(const dl_ctx* c, int tile, int n, Batch& B) {
+  memset(&B, 0, sizeof(B));
+  long long item = 0;
+  int rhs = 0;
+  for (int l = 0; l < (int)c->lats.size(); ++l) {
+    const LatInfo& LI = c->lats[l];
+    for (int k = 0; k * tile < n; ++k) {
+      if (B.nlat >= DL_MAX_LAT) return false;
+      LatDesc& L = B.lat[B.nlat++];
+      L.X = LI.dims[0];
+      L.Y = LI.dims[1];
+      L.Z = LI.dims[2];
+      L.T = LI.dims[3];
+      L.Vh = LI.Vh;
+      L.lognpad = ilog2ceil(tile);
+      L.ncol = std::min(tile, n - k * tile);
+      L.rhs_base = rhs;
+      L.item_off = item;
+      L.gsite_off = LI.gsite_off;
+      L.tbc = LI.tbc;
+      L.kappa = LI.kappa;
+      L.amu = LI.amu;
+      L.noise_base = (long long)l * n + (long long)k * tile;
+      rhs += L.ncol;
+      item += (long long)L.Vh << L.lognpad;
+    }
+  }
+  if (rhs > DL_NCMAX) return false;
+  B.pstride = (int)c->partial_blocks;
+  // more than 32 padded columns per lattice would overrun the partial-sum buffer
+  return (size_t)dl::blocks_for(B, 256) <= c->partial_blocks;
+}
+
+// Site factor T = a + i b gamma_5 of R_f (inv = false) or R_f^{-1} (inv = true) for
+// one lattice's kappa and a*mu.
+void twist_ab_l(const LatDesc& L, int f, bool inv, double& a, double& b) {
+  double w = 2.0 * L.kappa * L.amu * f;
   if (!inv) {
     a = 1.0;
     b = w;
@@ -144,19 +110,41 @@ void twist_ab(const dl_ctx* c, int f, bool inv, double& a, double& b) {
   }
 }
 
-// kinds of site factor: 0 identity, 1 R_f, 2 R_f^{-1}
-EpiSet epi(const dl_ctx* c, double coef, int t1, int f1, int t2, int f2) {
+// Epilogue coefficient kinds, evaluated per lattice of a batch.
+
+// kinds of site factor: 0 identity, 1 R_f, 2 R_f^{-1}; every lattice of B gets its own
+EpiSet epiB(const Batch& B, int ck, int t1, int f1, int t2, int f2) {
   EpiSet E;
   memset(&E, 0, sizeof(E));
-  Epi& e = E.e[0];
-  e.c = coef;
-  e.a1 = 1.0;
-  e.b1 = 0.0;
-  e.a2 = 1.0;
-  e.b2 = 0.0;
-  if (t1) twist_ab(c, f1, t1 == 2, e.a1, e.b1);
-  if (t2) twist_ab(c, f2, t2 == 2, e.a2, e.b2);
+  for (int l = 0; l < B.nlat; ++l) {
+    const LatDesc& L = B.lat[l];
+    Epi& e = E.e[l];
+    e.c = ck == CK_ONE ? 1.0 : (ck == CK_K ? L.kappa : (ck == CK_MK ? -L.kappa : -L.kappa * L.kappa));
+    e.a1 = 1.0;
+    e.b1 = 0.0;
+    e.a2 = 1.0;
+    e.b2 = 0.0;
+    if (t1) twist_ab_l(L, f1, t1 == 2, e.a1, e.b1);
+    if (t2) twist_ab_l(L, f2, t2 == 2, e.a2, e.b2);
+    e.cf = (float)e.c;
+    e.a1f = (float)e.a1;
+    e.b1f = (float)e.b1;
+    e.a2f = (float)e.a2;
+    e.b2f = (float)e.b2;
+  }
   return E;
+}
+
+int ncols_of(const Batch& B) {
+  int n = 0;
+  for (int l = 0; l < B.nlat; ++l) n += B.lat[l].ncol;
+  return n;
+}
+
+size_t items_of(const Batch& B) {
+  size_t n = 0;
+  for (int l = 0; l < B.nlat; ++l) n += (size_t)B.lat[l].Vh << B.lat[l].lognpad;
+  return n;
 }
 
 int grec_of(const dl_ctx* c, int prec) { return prec == P64 ? 18 : (prec == P32 ? c->rec32 : c->rec16); }
@@ -167,8 +155,8 @@ void invalidate_graphs(dl_ctx* c) {
   c->graphs.clear();
 }
 
-dl_status ensure_field(dl_ctx* c, const std::string& base, int prec, int ncol, Field** out) {
-  size_t items = (size_t)c->Vh << ilog2ceil(std::max(ncol, 1));
+dl_status ensure_field(dl_ctx* c, const std::string& base, int prec, const Batch& B, Field** out) {
+  const size_t items = items_of(B);
   const std::string name = base + "#" + std::to_string(prec);
   auto it = c->ws.find(name);
   if (it != c->ws.end() && it->second.prec == prec && it->second.items >= items) {
@@ -246,7 +234,7 @@ const FieldRef NOF = {nullptr, nullptr};
 // out_o = R_{f'}^{-1} D^{(dag)}_oe in_e,  f' = dag ? -f : f
 cudaError_t stage1(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRef in_e, FieldRef out_o, const int* mask) {
   int ff = dag ? -f : f;
-  EpiSet E = epi(c, 1.0, 2, ff, 0, 0);
+  EpiSet E = epiB(B, CK_ONE, 2, ff, 0, 0);
   GaugeSet g{c->g64, c->g32, c->g16};
   return dl::dslash(B, prec, grec_of(c, prec), EPI_PLAIN, dag, 1, in_e, NOF, out_o, g, E, mask, nullptr, NOF, NOF, NOF,
                     nullptr, c->st);
@@ -255,7 +243,7 @@ cudaError_t stage1(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRe
 cudaError_t stage2(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRef in_o, FieldRef aux_e, FieldRef out_e,
                    const int* mask, double* partial) {
   int ff = dag ? -f : f;
-  EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, ff);
+  EpiSet E = epiB(B, CK_MK2, 0, 0, 1, ff);
   GaugeSet g{c->g64, c->g32, c->g16};
   return dl::dslash(B, prec, grec_of(c, prec), partial ? EPI_AUX_NORM : EPI_AUX, dag, 0, in_o, aux_e, out_e, g, E, mask,
                     partial, NOF, NOF, NOF, nullptr, c->st);
@@ -272,7 +260,7 @@ cudaError_t normal_op(dl_ctx* c, const Batch& B, int prec, int f, FieldRef x, Fi
 
 // per-column sums of the partial buffer into S[slot]
 cudaError_t colsum(dl_ctx* c, const Batch& B, int slot) {
-  return dl::sum_partials(B, c->partial, c->S, DL_NCMAX, slot, B.lat[0].ncol, c->st);
+  return dl::sum_partials(B, c->partial, c->S, DL_NCMAX, slot, ncols_of(B), c->st);
 }
 
 // ---- the CG on the normal equations ----------------------------------------
@@ -309,14 +297,14 @@ struct CGFields {
 
 // One CG iteration for all active columns (low precision); graph-capturable.
 cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta) {
-  const int n = B.lat[0].ncol;
+  const int n = ncols_of(B);
   DL_CUDA_TRY(stage1(c, B, lo, false, f, F.p->ref(), F.t1->ref(), c->active));
   DL_CUDA_TRY(stage2(c, B, lo, false, f, F.t1->ref(), F.p->ref(), F.q->ref(), c->active, c->partial));
   DL_CUDA_TRY(colsum(c, B, DL_S_PAP));
   DL_CUDA_TRY(dl::cg_alpha(n, c->S, c->active, c->flags, c->st));
   DL_CUDA_TRY(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), c->active));
   {
-    EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, -f);
+    EpiSet E = epiB(B, CK_MK2, 0, 0, 1, -f);
     GaugeSet g{c->g64, c->g32, c->g16};
     DL_CUDA_TRY(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, c->active,
                            c->partial, F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
@@ -342,7 +330,7 @@ dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGField
   CK(cudaEventRecord(ev[4], c->st));
   CK(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), nullptr));
   CK(cudaEventRecord(ev[5], c->st));
-  EpiSet E = epi(c, -c->kappa * c->kappa, 0, 0, 1, -f);
+  EpiSet E = epiB(B, CK_MK2, 0, 0, 1, -f);
   CK(cudaEventRecord(ev[6], c->st));
   CK(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, nullptr, c->partial,
                 F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
@@ -353,7 +341,9 @@ dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGField
     CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
     c->prof_ms[k][lo] += ms;
     c->prof_n[k][lo] += 1;
-    c->prof_items[k][lo] += (long long)c->Vh * B.lat[0].ncol;
+    long long it = 0;
+    for (int l = 0; l < B.nlat; ++l) it += (long long)B.lat[l].Vh * B.lat[l].ncol;
+    c->prof_items[k][lo] += it;  // site-column items with every column active
   }
   return DL_OK;
 }
@@ -362,7 +352,7 @@ dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGField
 // r_hi = b - A x (high precision), r = r_hi.  Returns |r_hi|^2 per column.
 dl_status reliable_update(dl_ctx* c, const Batch& B, int hi, int lo, int f, const CGFields& F, Field* x, Field* b,
                           const std::vector<int>& mask, std::vector<double>& rr_true) {
-  const int n = B.lat[0].ncol;
+  const int n = ncols_of(B);
   CK(cudaMemcpyAsync(c->upd, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
   CK(dl::accum(B, hi, lo, x->ref(), F.y->ref(), c->upd, 1, c->st));
   CK(normal_op(c, B, hi, f, x->ref(), F.th1->ref(), F.tq->ref(), F.th2->ref(), F.ax->ref(), c->upd));
@@ -377,12 +367,18 @@ dl_status reliable_update(dl_ctx* c, const Batch& B, int hi, int lo, int f, cons
   return DL_OK;
 }
 
-std::string graph_key(const dl_ctx* c, int lo, int f, int n, double tol2, double delta, const CGFields& F) {
+std::string graph_key(const dl_ctx* c, const Batch& B, int lo, int f, double tol2, double delta, const CGFields& F) {
   char buf[512];
-  snprintf(buf, sizeof(buf), "%d|%d|%d|%.17g|%.17g|%.17g|%.17g|%p|%p|%p|%p|%p|%p|%p|%d|%d", lo, f, n, tol2, delta,
-           c->kappa, c->amu, F.r->data, F.p->data, F.y->data, F.t1->data, F.q->data, F.t2->data, (void*)c->partial,
-           c->rec32, c->rec16);
-  return std::string(buf);
+  snprintf(buf, sizeof(buf), "%d|%d|%.17g|%.17g|%p|%p|%p|%p|%p|%p|%p|%d|%d|", lo, f, tol2, delta, F.r->data, F.p->data,
+           F.y->data, F.t1->data, F.q->data, F.t2->data, (void*)c->partial, c->rec32, c->rec16);
+  std::string k(buf);
+  for (int l = 0; l < B.nlat; ++l) {
+    const LatDesc& L = B.lat[l];
+    snprintf(buf, sizeof(buf), "%d.%d.%d.%d.%d.%d.%lld.%lld.%.17g.%.17g.%.17g;", L.X, L.Y, L.Z, L.T, L.lognpad, L.ncol,
+             L.item_off, L.gsite_off, L.kappa, L.amu, L.tbc);
+    k += buf;
+  }
+  return k;
 }
 
 // The solver's graph: a conditional WHILE node whose body is one CG iteration
@@ -391,7 +387,7 @@ std::string graph_key(const dl_ctx* c, int lo, int f, int n, double tol2, double
 // limit (loopctr[1]) is reached.  One launch runs as many iterations as needed.
 dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F, double tol2, double delta,
                     GraphEntry** out) {
-  std::string key = graph_key(c, lo, f, B.lat[0].ncol, tol2, delta, F);
+  std::string key = graph_key(c, B, lo, f, tol2, delta, F);
   for (auto& g : c->graphs)
     if (g.key == key) {
       *out = &g;
@@ -412,7 +408,8 @@ dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F,
   const long long before = g_launches.load();
   CK(cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cg_iteration(c, B, lo, f, F, tol2, delta);
-  if (e == cudaSuccess) e = dl::cg_cond(B.lat[0].ncol, c->active, c->flags, c->loopctr, c->loopctr + 1, c->waitc, h, c->st);
+  if (e == cudaSuccess)
+    e = dl::cg_cond(ncols_of(B), c->active, c->flags, c->loopctr, c->loopctr + 1, c->waitc, h, nullptr, c->st);
   cudaGraph_t captured;
   cudaError_t e2 = cudaStreamEndCapture(c->st, &captured);
   if (e != cudaSuccess) {
@@ -436,20 +433,20 @@ dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F,
 
 // Solve Mhat^dag Mhat x = b (b: normal-equation rhs in hi precision) for n columns.
 // x (hi) receives the solution.  final_check recomputes the residual in hi.
-dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* x, bool final_check,
+dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b, Field* x, bool final_check,
                  dl_solve_stats* stats, double* resid_out) {
   const int hi = prm.prec_hi, lo = prm.prec_lo, f = prm.flavour;
-  Batch B = make_batch(c, n);
+  const int n = ncols_of(B);
   dl_status s;
   if ((s = ensure_partial(c, B)) != DL_OK) return s;
   CGFields F;
   const int lo_ = lo;
-  if ((s = ensure_field(c, "cg_r", lo_, n, &F.r)) || (s = ensure_field(c, "cg_p", lo_, n, &F.p)) ||
-      (s = ensure_field(c, "cg_y", lo_, n, &F.y)) || (s = ensure_field(c, "cg_t1", lo_, n, &F.t1)) ||
-      (s = ensure_field(c, "cg_q", lo_, n, &F.q)) || (s = ensure_field(c, "cg_t2", lo_, n, &F.t2)) ||
-      (s = ensure_field(c, "cg_rh", hi, n, &F.rh)) || (s = ensure_field(c, "cg_ax", hi, n, &F.ax)) ||
-      (s = ensure_field(c, "cg_th1", hi, n, &F.th1)) || (s = ensure_field(c, "cg_tq", hi, n, &F.tq)) ||
-      (s = ensure_field(c, "cg_th2", hi, n, &F.th2)))
+  if ((s = ensure_field(c, "cg_r", lo_, B, &F.r)) || (s = ensure_field(c, "cg_p", lo_, B, &F.p)) ||
+      (s = ensure_field(c, "cg_y", lo_, B, &F.y)) || (s = ensure_field(c, "cg_t1", lo_, B, &F.t1)) ||
+      (s = ensure_field(c, "cg_q", lo_, B, &F.q)) || (s = ensure_field(c, "cg_t2", lo_, B, &F.t2)) ||
+      (s = ensure_field(c, "cg_rh", hi, B, &F.rh)) || (s = ensure_field(c, "cg_ax", hi, B, &F.ax)) ||
+      (s = ensure_field(c, "cg_th1", hi, B, &F.th1)) || (s = ensure_field(c, "cg_tq", hi, B, &F.tq)) ||
+      (s = ensure_field(c, "cg_th2", hi, B, &F.th2)))
     return s;
   // x = 0, |b|^2
   CK(dl::zero(B, hi, x->ref(), nullptr, c->st));
@@ -472,10 +469,10 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
   CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), nullptr, c->st));
   CK(dl::zero(B, lo, F.y->ref(), nullptr, c->st));
   const double tol2 = prm.tol * prm.tol;
-  GraphEntry* ge;
-  if ((s = get_graph(c, B, lo, f, F, tol2, prm.delta, &ge)) != DL_OK) return s;
-  const cudaGraphExec_t gexec = ge->exec;
-  const long long body_kernels = ge->kernels;
+  GraphEntry* ge = nullptr;
+  if (c->use_graphs && (s = get_graph(c, B, lo, f, F, tol2, prm.delta, &ge)) != DL_OK) return s;
+  const cudaGraphExec_t gexec = ge ? ge->exec : nullptr;
+  const long long body_kernels = ge ? ge->kernels : 0;
   std::vector<int> finalized(n, 0), notconv(n, 0);
   for (int i = 0; i < n; ++i)
     if (!h.active[i]) finalized[i] = 1;  // zero right-hand side: x = 0
@@ -491,11 +488,27 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
       if (h.active[i]) itmin = std::min(itmin, h.iters[i]);
     const int ctr[2] = {0, std::max(1, std::min(prm.max_iter - itmin, 1 << 20))};
     CK(cudaMemcpyAsync(c->loopctr, ctr, sizeof(ctr), cudaMemcpyHostToDevice, c->st));
-    CK(cudaGraphLaunch(gexec, c->st));
     int ran = 0;
-    CK(cudaMemcpyAsync(&ran, c->loopctr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    if ((s = download_state(c, n, h)) != DL_OK) return s;
-    g_launches.fetch_add(body_kernels * ran);
+    if (gexec) {
+      CK(cudaGraphLaunch(gexec, c->st));
+      CK(cudaMemcpyAsync(&ran, c->loopctr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      if ((s = download_state(c, n, h)) != DL_OK) return s;
+      g_launches.fetch_add(body_kernels * ran);
+    } else {
+      // the same body and loop condition launched from the host (profilers cannot
+      // see kernel nodes inside conditional graphs); one readback per iteration
+      int go = 1;
+      while (go) {
+        CK(cg_iteration(c, B, lo, f, F, tol2, prm.delta));
+        CK(dl::cg_cond(n, c->active, c->flags, c->loopctr, c->loopctr + 1, c->waitc, 0, c->loopctr + 2, c->st));
+        int hc[3];
+        CK(cudaMemcpyAsync(hc, c->loopctr, sizeof(hc), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        ran = hc[0];
+        go = hc[2];
+      }
+      if ((s = download_state(c, n, h)) != DL_OK) return s;
+    }
     std::vector<int> mask(n, 0);
     bool need = false;
     for (int i = 0; i < n; ++i) {
@@ -613,6 +626,8 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
   }
   if (resid_out)
     for (int i = 0; i < n; ++i) resid_out[i] = resid[i];
+  c->last_iters.assign(h.iters.begin(), h.iters.begin() + n);
+  c->last_resid = resid;
   if (breakdown) return DL_BREAKDOWN;
   if (anync) return fail(c, DL_NOT_CONVERGED, "max_iter reached");
   return DL_OK;
@@ -620,6 +635,7 @@ dl_status run_cg(dl_ctx* c, int n, const dl_solve_params& prm, Field* b, Field* 
 
 dl_status check_ctx(dl_ctx* c, bool need_gauge) {
   if (!c) return DL_ERR_ARG;
+  if (c->lats.size() != 1) return fail(c, DL_ERR_STATE, "this call works on single-lattice contexts; use dl_batch_loops");
   if (need_gauge && !c->has_gauge) return fail(c, DL_ERR_STATE, "no gauge field loaded");
   return DL_OK;
 }
@@ -629,29 +645,28 @@ int dtype_prec(int dtype) { return dtype == DL_C128 ? P64 : P32; }
 // ---- solve pipeline on internal fields --------------------------------------
 // From a full-lattice source (b_e, b_o, precision hi) to the solution
 // (x_e, psi_o, precision hi).
-dl_status solve_internal(dl_ctx* c, int n, const dl_solve_params& prm, Field* b_e, Field* b_o, Field* x_e, Field* psi_o,
-                         bool final_check, dl_solve_stats* stats) {
+dl_status solve_internal(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b_e, Field* b_o, Field* x_e,
+                         Field* psi_o, bool final_check, dl_solve_stats* stats) {
   const int hi = prm.prec_hi, f = prm.flavour;
-  Batch B = make_batch(c, n);
   dl_status s;
   Field *tmp_o, *bhat, *bn, *t2;
-  if ((s = ensure_field(c, "sv_tmp_o", hi, n, &tmp_o)) || (s = ensure_field(c, "sv_bhat", hi, n, &bhat)) ||
-      (s = ensure_field(c, "sv_bn", hi, n, &bn)) || (s = ensure_field(c, "sv_t2", hi, n, &t2)))
+  if ((s = ensure_field(c, "sv_tmp_o", hi, B, &tmp_o)) || (s = ensure_field(c, "sv_bhat", hi, B, &bhat)) ||
+      (s = ensure_field(c, "sv_bn", hi, B, &bn)) || (s = ensure_field(c, "sv_t2", hi, B, &t2)))
     return s;
   // bhat_e = b_e + kappa D_eo R_oo^{-1} b_o
-  EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+  EpiSet Ei = epiB(B, CK_ONE, 2, f, 0, 0);
   CK(dl::twist(B, hi, tmp_o->ref(), b_o->ref(), Ei, nullptr, c->st));
   GaugeSet g{c->g64, c->g32, c->g16};
-  EpiSet Ep = epi(c, c->kappa, 0, 0, 0, 0);
+  EpiSet Ep = epiB(B, CK_K, 0, 0, 0, 0);
   CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, tmp_o->ref(), b_e->ref(), bhat->ref(), g, Ep, nullptr, nullptr,
                 NOF, NOF, NOF, nullptr, c->st));
   // bn = Mhat^dag bhat
   CK(stage1(c, B, hi, true, f, bhat->ref(), t2->ref(), nullptr));
   CK(stage2(c, B, hi, true, f, t2->ref(), bhat->ref(), bn->ref(), nullptr, nullptr));
-  dl_status rs = run_cg(c, n, prm, bn, x_e, final_check, stats, nullptr);
+  dl_status rs = run_cg(c, B, prm, bn, x_e, final_check, stats, nullptr);
   if (rs < 0) return rs;
   // psi_o = R_oo^{-1} (b_o + kappa D_oe x_e)
-  EpiSet Er = epi(c, c->kappa, 2, f, 0, 0);
+  EpiSet Er = epiB(B, CK_K, 2, f, 0, 0);
   CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 1, x_e->ref(), b_o->ref(), psi_o->ref(), g, Er, nullptr, nullptr,
                 NOF, NOF, NOF, nullptr, c->st));
   return rs;
@@ -681,9 +696,11 @@ int mom_extent(int p2max) {
 
 // Contract (s_e, s_o) with (eta_e, eta_o) for estimator mode into out
 // [ncol][T][np][nd][16] (device complex128) with the prefactor applied.
-dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv, int p2max, Field* s_e, Field* s_o,
-                            Field* eta_e, Field* eta_o, double pre_re, double pre_im, double2* out, int accumulate) {
-  Batch B = make_batch(c, n);
+// B must describe one lattice segment (B.nlat == 1); its fields are read at the
+// segment's offsets.
+dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int with_deriv, int p2max, Field* s_e,
+                            Field* s_o, Field* eta_e, Field* eta_o, double pre_re, double pre_im, double2* out,
+                            int accumulate) {
   const LatDesc& L = B.lat[0];
   dl_status s;
   if ((s = ensure_momenta(c, p2max)) != DL_OK) return s;
@@ -706,10 +723,10 @@ dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv
   double2* G3 = G2 + nG2;
   double2* ph = G3 + nG3;
   if (L.X > (int)nph || L.Y > (int)nph || L.Z > (int)nph) return fail(c, DL_ERR_ARG, "spatial extent too large");
-  const int fp32 = prec != P64;
+  const int fp32 = fused && prec != P64;  // the unfused fallback keeps every stage in FP64
   if (fused) {
     CK(dl::contract_x(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
-                      eta_o ? eta_o->ref() : NOF, c->g64, mx, G1, c->st));
+                      eta_o ? eta_o->ref() : NOF, c->g64, c->g32, c->rec32, mx, G1, c->st));
   } else {
     CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
                           eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
@@ -717,20 +734,19 @@ dl_status contract_internal(dl_ctx* c, int n, int prec, int mode, int with_deriv
   }
   CK(dl::dft_pass(G1, G2, (long long)ncomp * L.T * L.Z, L.Y, (long long)NX * npad, my, ph, fp32, c->st));
   CK(dl::dft_pass(G2, G3, (long long)ncomp * L.T, L.Z, (long long)NY * NX * npad, mz, ph, fp32, c->st));
-  CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, pre_re, pre_im, out, accumulate, c->st));
+  CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, fp32, pre_re, pre_im, out, accumulate, c->st));
   return DL_OK;
 }
 
 // w = (BH)^k s on the full lattice, B = R_f^{-1}, H = -kappa D (Eq. HPE)
-dl_status bh_power(dl_ctx* c, int n, int prec, int f, int k, Field* se, Field* so, Field** we, Field** wo) {
-  Batch B = make_batch(c, n);
+dl_status bh_power(dl_ctx* c, const Batch& B, int prec, int f, int k, Field* se, Field* so, Field** we, Field** wo) {
   dl_status s;
   Field *ae, *ao, *be, *bo;
-  if ((s = ensure_field(c, "bh_ae", prec, n, &ae)) || (s = ensure_field(c, "bh_ao", prec, n, &ao)) ||
-      (s = ensure_field(c, "bh_be", prec, n, &be)) || (s = ensure_field(c, "bh_bo", prec, n, &bo)))
+  if ((s = ensure_field(c, "bh_ae", prec, B, &ae)) || (s = ensure_field(c, "bh_ao", prec, B, &ao)) ||
+      (s = ensure_field(c, "bh_be", prec, B, &be)) || (s = ensure_field(c, "bh_bo", prec, B, &bo)))
     return s;
   GaugeSet g{c->g64, c->g32, c->g16};
-  EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+  EpiSet E = epiB(B, CK_MK, 2, f, 0, 0);
   Field *ie = se, *io = so;
   for (int it = 0; it < k; ++it) {
     Field* oe = (it % 2 == 0) ? ae : be;
@@ -747,24 +763,45 @@ dl_status bh_power(dl_ctx* c, int n, int prec, int f, int k, Field* se, Field* s
   return DL_OK;
 }
 
-}  // namespace
+}  // namespace dlh
+
+using namespace dlh;
 
 // ============================================================================
 extern "C" {
 
-dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stream) {
-  if (!out || !dims) return DL_ERR_ARG;
+static dl_status create_ctx(dl_ctx** out, int nlat, const int* dims, int device, void* cuda_stream) {
+  if (!out || !dims || nlat < 1 || nlat > DL_MAX_LAT) return DL_ERR_ARG;
   *out = nullptr;
-  for (int k = 0; k < 4; ++k)
-    if (dims[k] < 2 || (dims[k] & 1)) return DL_ERR_ARG;
-  long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
-  if (V / 2 >= (1LL << 31) / DL_MAXC) return DL_ERR_ARG;
+  long long Vt = 0;
+  for (int l = 0; l < nlat; ++l) {
+    for (int k = 0; k < 4; ++k)
+      if (dims[4 * l + k] < 2 || (dims[4 * l + k] & 1)) return DL_ERR_ARG;
+    Vt += (long long)dims[4 * l] * dims[4 * l + 1] * dims[4 * l + 2] * dims[4 * l + 3] / 2;
+  }
+  if (Vt >= (1LL << 31) / DL_MAXC) return DL_ERR_ARG;
   dl_ctx* c = new dl_ctx();
   c->dev = device;
+  long long off = 0;
+  for (int l = 0; l < nlat; ++l) {
+    LatInfo L;
+    memcpy(L.dims, dims + 4 * l, sizeof(int) * 4);
+    L.Vh = (int)((long long)L.dims[0] * L.dims[1] * L.dims[2] * L.dims[3] / 2);
+    L.gsite_off = off;
+    off += L.Vh;
+    c->lats.push_back(L);
+  }
+  c->Vh_total = Vt;
   memcpy(c->dims, dims, sizeof(int) * 4);
-  c->Vh = (int)(V / 2);
-  c->partial_blocks = ((size_t)c->Vh * DL_MAXC + 255) / 256 + 8;
+  c->Vh = c->lats[0].Vh;
+  // blocks of any launch: 256-thread blocks over <= 32 columns of every site, one
+  // ragged block per lattice segment
+  c->partial_blocks = ((size_t)Vt * DL_MAXC + 255) / 256 + 2 * DL_MAX_LAT + 8;
   c->user = (cudaStream_t)cuda_stream;
+  {
+    const char* gv = getenv("DL_GRAPHS");  // "0": launch the CG loop from the host (for profilers)
+    c->use_graphs = !(gv && gv[0] == '0');
+  }
   cudaError_t e;
   if ((e = cudaSetDevice(device)) != cudaSuccess || (e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming)) != cudaSuccess ||
@@ -775,20 +812,27 @@ dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stre
       (e = cudaMalloc((void**)&c->iters, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->upd, sizeof(int) * DL_NCMAX)) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->misc, sizeof(double2) * 4096)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&c->partial, sizeof(double) * DL_MAXC * (((size_t)c->Vh * DL_MAXC + 255) / 256 + 8))) !=
-          cudaSuccess ||
-      (e = cudaMalloc((void**)&c->loopctr, 2 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->partial, sizeof(double) * DL_MAXC * c->partial_blocks)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&c->loopctr, 3 * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc((void**)&c->waitc, DL_NCMAX * sizeof(int))) != cudaSuccess) {
     dl_destroy(c);
     return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
   }
   for (int k = 0; k < 8; ++k)
     if ((e = cudaEventCreate(&c->pev[k])) != cudaSuccess) {
-    dl_destroy(c);
-    return e == cudaErrorMemoryAllocation ? DL_ERR_OOM : DL_ERR_CUDA;
-  }
+      dl_destroy(c);
+      return DL_ERR_CUDA;
+    }
   *out = c;
   return DL_OK;
+}
+
+dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stream) {
+  return create_ctx(out, 1, dims, device, cuda_stream);
+}
+
+dl_status dl_create_multi(dl_ctx** out, int nlat, const int* dims, int device, void* cuda_stream) {
+  return create_ctx(out, nlat, dims, device, cuda_stream);
 }
 
 void dl_destroy(dl_ctx* c) {
@@ -822,20 +866,26 @@ dl_status dl_set_stream(dl_ctx* c, void* s) {
   return DL_OK;
 }
 
-dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_boundary, int recon_f32, int recon_f16) {
-  if (!c || !links) return DL_ERR_ARG;
+dl_status dl_load_gauge_lat(dl_ctx* c, int lat, const double* links, int on_device, double t_boundary, int recon_f32,
+                            int recon_f16) {
+  if (!c || !links || lat < 0 || lat >= (int)c->lats.size()) return DL_ERR_ARG;
   if (!(recon_f32 == 12 || recon_f32 == 8 || recon_f32 == 18)) return fail(c, DL_ERR_ARG, "recon_f32 must be 18, 12 or 8");
   if (!(recon_f16 == 12 || recon_f16 == 8)) return fail(c, DL_ERR_ARG, "recon_f16 must be 12 or 8");
   if (recon_f32 == 18) recon_f32 = 12;  // FP32 operator reads the 12-real form; 18 is accepted as "uncompressed request"
+  bool any = false;
+  for (auto& L : c->lats) any |= L.has_gauge;
+  if (any && (recon_f32 != c->rec32 || recon_f16 != c->rec16))
+    return fail(c, DL_ERR_ARG, "every lattice of a context uses the same link compression");
   dl_status s;
   if ((s = enter(c)) != DL_OK) return s;
-  const size_t V = 2ull * c->Vh;
-  const size_t nl = V * 4;
+  const size_t nl_total = 2ull * c->Vh_total * 4;
   if (!c->g64) {
-    CK(cudaMalloc(&c->g64, nl * 9 * sizeof(double2)));  // 144 B per link
-    CK(cudaMalloc(&c->g32, nl * 3 * sizeof(float4)));    // up to 48 B per link
-    CK(cudaMalloc(&c->g16, nl * 3 * sizeof(uint2)));     // up to 24 B per link
+    CK(cudaMalloc(&c->g64, nl_total * 9 * sizeof(double2)));  // 144 B per link
+    CK(cudaMalloc(&c->g32, nl_total * 3 * sizeof(float4)));    // up to 48 B per link
+    CK(cudaMalloc(&c->g16, nl_total * 3 * sizeof(uint2)));     // up to 24 B per link
   }
+  LatInfo& LI = c->lats[lat];
+  const size_t nl = 2ull * LI.Vh * 4;
   const double* dlinks = links;
   void* tmp = nullptr;
   if (!on_device) {
@@ -843,37 +893,69 @@ dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_
     CK(cudaMemcpyAsync(tmp, links, nl * 9 * sizeof(double2), cudaMemcpyHostToDevice, c->st));
     dlinks = (const double*)tmp;
   }
-  c->tbc = t_boundary;
+  LI.tbc = t_boundary;
   c->rec32 = recon_f32;
   c->rec16 = recon_f16;
-  Batch B = make_batch(c, 1);
-  cudaError_t e = dl::pack_gauge(B.lat[0], dlinks, c->g64, c->g32, recon_f32, c->g16, recon_f16, c->st);
+  LatDesc L;
+  memset(&L, 0, sizeof(L));
+  L.X = LI.dims[0];
+  L.Y = LI.dims[1];
+  L.Z = LI.dims[2];
+  L.T = LI.dims[3];
+  L.Vh = LI.Vh;
+  // byte offsets of this lattice in each gauge array (chunk bytes x chunks per link x 8 links per parity site)
+  const size_t o = (size_t)LI.gsite_off;
+  char* g64 = (char*)c->g64 + o * 16 * 9 * 8;
+  char* g32 = (char*)c->g32 + o * 16 * (recon_f32 == 12 ? 3 : 2) * 8;
+  char* g16 = (char*)c->g16 + o * (recon_f16 == 12 ? 8 * 3 : 16 * 1) * 8;
+  cudaError_t e = dl::pack_gauge(L, dlinks, g64, g32, recon_f32, g16, recon_f16, c->st);
   if (tmp) {
     cudaStreamSynchronize(c->st);
     cudaFree(tmp);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "pack_gauge");
+  LI.has_gauge = true;
+  if (lat == 0) c->tbc = t_boundary;
   c->has_gauge = true;
+  for (auto& Lx : c->lats) c->has_gauge = c->has_gauge && Lx.has_gauge;
   invalidate_graphs(c);
   return leave(c);
 }
 
+dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_boundary, int recon_f32, int recon_f16) {
+  return dl_load_gauge_lat(c, 0, links, on_device, t_boundary, recon_f32, recon_f16);
+}
+
+dl_status dl_set_params_lat(dl_ctx* c, int lat, double kappa, double amu) {
+  if (!c || lat < 0 || lat >= (int)c->lats.size()) return DL_ERR_ARG;
+  if (!(kappa > 0.0) || !std::isfinite(kappa) || !std::isfinite(amu)) return fail(c, DL_ERR_ARG, "bad kappa/amu");
+  c->lats[lat].kappa = kappa;
+  c->lats[lat].amu = amu;
+  if (lat == 0) {
+    c->kappa = kappa;
+    c->amu = amu;
+  }
+  return DL_OK;
+}
+
 dl_status dl_set_params(dl_ctx* c, double kappa, double amu) {
   if (!c) return DL_ERR_ARG;
-  if (!(kappa > 0.0) || !std::isfinite(kappa) || !std::isfinite(amu)) return fail(c, DL_ERR_ARG, "bad kappa/amu");
-  c->kappa = kappa;
-  c->amu = amu;
+  for (int l = 0; l < (int)c->lats.size(); ++l) {
+    dl_status s = dl_set_params_lat(c, l, kappa, amu);
+    if (s != DL_OK) return s;
+  }
   return DL_OK;
 }
 
 dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant) {
   if (!c || !out || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64)) return DL_ERR_ARG;
   dl_status s;
+  if ((s = check_ctx(c, false)) != DL_OK) return s;
   if ((s = enter(c)) != DL_OK) return s;
   const int prec = dtype_prec(dtype);
   Batch B = make_batch(c, n);
   Field *e, *o;
-  if ((s = ensure_field(c, "nz_e", prec, n, &e)) || (s = ensure_field(c, "nz_o", prec, n, &o))) return s;
+  if ((s = ensure_field(c, "nz_e", prec, B, &e)) || (s = ensure_field(c, "nz_o", prec, B, &o))) return s;
   CK(dl::noise_z4(B, prec, 0, e->ref(), seed, first_index, quadrant, c->st));
   CK(dl::noise_z4(B, prec, 1, o->ref(), seed, first_index, quadrant, c->st));
   CK(dl::unpack(B, prec, 0, out, e->ref(), dtype, c->st));
@@ -892,10 +974,10 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
   Batch B = make_batch(c, n);
   if ((s = ensure_partial(c, B)) != DL_OK) return s;
   Field *ie, *io, *oe, *oo, *ae, *ao, *t;
-  if ((s = ensure_field(c, "ap_ie", prec, n, &ie)) || (s = ensure_field(c, "ap_io", prec, n, &io)) ||
-      (s = ensure_field(c, "ap_oe", prec, n, &oe)) || (s = ensure_field(c, "ap_oo", prec, n, &oo)) ||
-      (s = ensure_field(c, "ap_ae", prec, n, &ae)) || (s = ensure_field(c, "ap_ao", prec, n, &ao)) ||
-      (s = ensure_field(c, "ap_t", prec, n, &t)))
+  if ((s = ensure_field(c, "ap_ie", prec, B, &ie)) || (s = ensure_field(c, "ap_io", prec, B, &io)) ||
+      (s = ensure_field(c, "ap_oe", prec, B, &oe)) || (s = ensure_field(c, "ap_oo", prec, B, &oo)) ||
+      (s = ensure_field(c, "ap_ae", prec, B, &ae)) || (s = ensure_field(c, "ap_ao", prec, B, &ao)) ||
+      (s = ensure_field(c, "ap_t", prec, B, &t)))
     return s;
   CK(dl::pack(B, prec, 0, ie->ref(), in, dtype, c->st));
   CK(dl::pack(B, prec, 1, io->ref(), in, dtype, c->st));
@@ -913,13 +995,13 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
     case DL_OP_M:
     case DL_OP_MDAG: {
       bool dag = op == DL_OP_MDAG;
-      EpiSet E = epi(c, -c->kappa, 0, 0, 1, dag ? -f : f);
+      EpiSet E = epiB(B, CK_MK, 0, 0, 1, dag ? -f : f);
       CK(D(EPI_AUX, dag, 0, io, ie, oe, E));
       CK(D(EPI_AUX, dag, 1, ie, io, oo, E));
       break;
     }
     case DL_OP_HOP: {
-      EpiSet E = epi(c, 1.0, 0, 0, 0, 0);
+      EpiSet E = epiB(B, CK_ONE, 0, 0, 0, 0);
       CK(D(EPI_PLAIN, false, 0, io, nullptr, oe, E));
       CK(D(EPI_PLAIN, false, 1, ie, nullptr, oo, E));
       break;
@@ -933,21 +1015,21 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
       break;
     }
     case DL_OP_PREP: {
-      EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+      EpiSet Ei = epiB(B, CK_ONE, 2, f, 0, 0);
       CK(dl::twist(B, prec, t->ref(), io->ref(), Ei, nullptr, c->st));
-      EpiSet E = epi(c, c->kappa, 0, 0, 0, 0);
+      EpiSet E = epiB(B, CK_K, 0, 0, 0, 0);
       CK(D(EPI_AUX, false, 0, t, ie, oe, E));
       CK(dl::zero(B, prec, oo->ref(), nullptr, c->st));
       break;
     }
     case DL_OP_RECON: {
       CK(dl::copy(B, prec, prec, oe->ref(), ie->ref(), nullptr, c->st));
-      EpiSet E = epi(c, c->kappa, 2, f, 0, 0);
+      EpiSet E = epiB(B, CK_K, 2, f, 0, 0);
       CK(D(EPI_AUX, false, 1, ie, ao, oo, E));
       break;
     }
     case DL_OP_BH: {
-      EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+      EpiSet E = epiB(B, CK_MK, 2, f, 0, 0);
       CK(D(EPI_PLAIN, false, 0, io, nullptr, oe, E));
       CK(D(EPI_PLAIN, false, 1, ie, nullptr, oo, E));
       break;
@@ -975,14 +1057,14 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
   Batch B = make_batch(c, n);
   if ((s = ensure_partial(c, B)) != DL_OK) return s;
   Field *be, *bo, *xe, *po;
-  if ((s = ensure_field(c, "sl_be", hi, n, &be)) || (s = ensure_field(c, "sl_bo", hi, n, &bo)) ||
-      (s = ensure_field(c, "sl_xe", hi, n, &xe)) || (s = ensure_field(c, "sl_po", hi, n, &po)))
+  if ((s = ensure_field(c, "sl_be", hi, B, &be)) || (s = ensure_field(c, "sl_bo", hi, B, &bo)) ||
+      (s = ensure_field(c, "sl_xe", hi, B, &xe)) || (s = ensure_field(c, "sl_po", hi, B, &po)))
     return s;
   CK(dl::pack(B, hi, 0, be->ref(), src, dtype, c->st));
   CK(dl::pack(B, hi, 1, bo->ref(), src, dtype, c->st));
   dl_solve_stats st;
   memset(&st, 0, sizeof(st));
-  dl_status rs = solve_internal(c, n, *prm, be, bo, xe, po, true, &st);
+  dl_status rs = solve_internal(c, B, *prm, be, bo, xe, po, true, &st);
   if (rs < 0) return rs;
   CK(dl::unpack(B, hi, 0, sol, xe->ref(), dtype, c->st));
   CK(dl::unpack(B, hi, 1, sol, po->ref(), dtype, c->st));
@@ -990,13 +1072,13 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
   // precision with FP64 reductions
   {
     Field *bh_e, *bh_o, *re, *ro;
-    if ((s = ensure_field(c, "tr_be", hi, n, &bh_e)) || (s = ensure_field(c, "tr_bo", hi, n, &bh_o)) ||
-        (s = ensure_field(c, "tr_re", hi, n, &re)) || (s = ensure_field(c, "tr_ro", hi, n, &ro)))
+    if ((s = ensure_field(c, "tr_be", hi, B, &bh_e)) || (s = ensure_field(c, "tr_bo", hi, B, &bh_o)) ||
+        (s = ensure_field(c, "tr_re", hi, B, &re)) || (s = ensure_field(c, "tr_ro", hi, B, &ro)))
       return s;
     CK(dl::pack(B, hi, 0, bh_e->ref(), src, dtype, c->st));
     CK(dl::pack(B, hi, 1, bh_o->ref(), src, dtype, c->st));
     GaugeSet g{c->g64, c->g32, c->g16};
-    EpiSet E = epi(c, -c->kappa, 0, 0, 1, prm->flavour);
+    EpiSet E = epiB(B, CK_MK, 0, 0, 1, prm->flavour);
     CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, po->ref(), xe->ref(), re->ref(), g, E, nullptr, nullptr, NOF,
                   NOF, NOF, nullptr, c->st));
     CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 1, xe->ref(), po->ref(), ro->ref(), g, E, nullptr, nullptr, NOF,
@@ -1082,8 +1164,8 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
   const int prec = dtype_prec(dtype);
   Batch B = make_batch(c, n);
   Field *se, *so, *ee, *eo;
-  if ((s = ensure_field(c, "ct_se", prec, n, &se)) || (s = ensure_field(c, "ct_so", prec, n, &so)) ||
-      (s = ensure_field(c, "ct_ee", prec, n, &ee)) || (s = ensure_field(c, "ct_eo", prec, n, &eo)))
+  if ((s = ensure_field(c, "ct_se", prec, B, &se)) || (s = ensure_field(c, "ct_so", prec, B, &so)) ||
+      (s = ensure_field(c, "ct_ee", prec, B, &ee)) || (s = ensure_field(c, "ct_eo", prec, B, &eo)))
     return s;
   CK(dl::pack(B, prec, 0, se->ref(), sol, dtype, c->st));
   CK(dl::pack(B, prec, 1, so->ref(), sol, dtype, c->st));
@@ -1096,7 +1178,7 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
   }
   Field *we = se, *wo = so;
   if (est == DL_EST_HPE)
-    if ((s = bh_power(c, n, prec, 1, 4, se, so, &we, &wo)) != DL_OK) return s;
+    if ((s = bh_power(c, B, prec, 1, 4, se, so, &we, &wo)) != DL_OK) return s;
   double pre_re = 1.0, pre_im = 0.0;
   if (est == DL_EST_ONE_END) {
     pre_re = 0.0;
@@ -1104,7 +1186,7 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
   } else if (est == DL_EST_GEN) {
     pre_re = 2.0;
   }
-  if ((s = contract_internal(c, n, prec, est, with_deriv, p2max, we, wo, ee, eo, pre_re, pre_im, (double2*)out,
+  if ((s = contract_internal(c, B, prec, est, with_deriv, p2max, we, wo, ee, eo, pre_re, pre_im, (double2*)out,
                              accumulate)) != DL_OK)
     return s;
   return leave(c);
@@ -1192,15 +1274,16 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     if ((s2 = ensure_partial(c, B)) != DL_OK) return s2;
     Field *ee, *eo, *xe, *po;
     const char* tag = hp ? "64" : "32";
-    if ((s2 = ensure_field(c, std::string("ts_ee") + tag, hi, n, &ee)) ||
-        (s2 = ensure_field(c, std::string("ts_eo") + tag, hi, n, &eo)) ||
-        (s2 = ensure_field(c, std::string("ts_xe") + tag, hi, n, &xe)) ||
-        (s2 = ensure_field(c, std::string("ts_po") + tag, hi, n, &po)))
+    if ((s2 = ensure_field(c, std::string("ts_ee") + tag, hi, B, &ee)) ||
+        (s2 = ensure_field(c, std::string("ts_eo") + tag, hi, B, &eo)) ||
+        (s2 = ensure_field(c, std::string("ts_xe") + tag, hi, B, &xe)) ||
+        (s2 = ensure_field(c, std::string("ts_po") + tag, hi, B, &po)))
       return s2;
     CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, first, 0, c->st));
     CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, first, 0, c->st));
     auto t0 = std::chrono::steady_clock::now();
-    dl_status rs = solve_internal(c, n, sp, ee, eo, xe, po, false, st);
+    dl_status rs = (!hp && prm->lp_net) ? nn_map_block(prm->lp_net, c, B, ee, eo, xe, po)
+                                        : solve_internal(c, B, sp, ee, eo, xe, po, false, st);
     if (rs < 0) return rs;
     if (rs == DL_NOT_CONVERGED) any_nc = true;
     CK(cudaStreamSynchronize(c->st));
@@ -1210,8 +1293,8 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
       double2* o = out + (size_t)e * per * blk;
       if (est_mode[e] == DL_EST_HPE) {
         Field *we, *wo;
-        if ((s2 = bh_power(c, n, hi, 1, 4, xe, po, &we, &wo)) != DL_OK) return s2;
-        if ((s2 = contract_internal(c, n, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0)) != DL_OK) return s2;
+        if ((s2 = bh_power(c, B, hi, 1, 4, xe, po, &we, &wo)) != DL_OK) return s2;
+        if ((s2 = contract_internal(c, B, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0)) != DL_OK) return s2;
         CK(dl::add_exact_p0(B, np, nd, ip0, c->misc, Ls, o, c->st));
       } else {
         double pr = 1.0, pi = 0.0;
@@ -1221,7 +1304,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
         } else {
           pr = 2.0;
         }
-        if ((s2 = contract_internal(c, n, hi, est_mode[e], prm->with_deriv, prm->p2max, xe, po, ee, eo, pr, pi, o, 0)) !=
+        if ((s2 = contract_internal(c, B, hi, est_mode[e], prm->with_deriv, prm->p2max, xe, po, ee, eo, pr, pi, o, 0)) !=
             DL_OK)
           return s2;
       }
@@ -1285,6 +1368,141 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
   }
   if ((s = leave(c)) != DL_OK) return s;
   return any_nc ? fail(c, DL_NOT_CONVERGED, "a TSM solve hit max_iter") : DL_OK;
+}
+
+dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, void* sol, dl_batch_info* info) {
+  if (!c || !prm) return DL_ERR_ARG;
+  const int nl = (int)c->lats.size();
+  for (auto& L : c->lats)
+    if (!L.has_gauge) return fail(c, DL_ERR_STATE, "dl_batch_loops: a lattice has no gauge field");
+  const int n = prm->n;
+  if (n < 1 || n * nl > DL_NCMAX || !(prm->tol > 0.0) || prm->max_iter < 1 ||
+      !(prm->prec_hi == DL_F64 || prm->prec_hi == DL_F32) || prm->prec_lo < prm->prec_hi || prm->prec_lo > DL_F16 ||
+      prm->delta < 0.0 || prm->delta >= 1.0 ||
+      !(prm->tile == 0 || prm->tile == 4 || prm->tile == 8 || prm->tile == 16 || prm->tile == 32))
+    return fail(c, DL_ERR_ARG, "dl_batch_loops: bad parameters");
+  dl_status s;
+  if ((s = enter(c)) != DL_OK) return s;
+  const int hi = prm->prec_hi;
+  dl_batch_info inf;
+  memset(&inf, 0, sizeof(inf));
+  auto t0 = std::chrono::steady_clock::now();
+  // noise, source preparation and solve for every lattice in one batch
+  auto run = [&](int tile, int max_iter, double tol, double delta, Batch& B, Field** fe, bool* nc) -> dl_status {
+    if (!make_batch_multi(c, tile, n, B)) return fail(c, DL_ERR_ARG, "dl_batch_loops: too many instances for the tile");
+    dl_status s2;
+    Field *ee, *eo, *xe, *po;
+    if ((s2 = ensure_field(c, "bt_ee", hi, B, &ee)) || (s2 = ensure_field(c, "bt_eo", hi, B, &eo)) ||
+        (s2 = ensure_field(c, "bt_xe", hi, B, &xe)) || (s2 = ensure_field(c, "bt_po", hi, B, &po)))
+      return s2;
+    CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, 0, 0, c->st));
+    CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, 0, 0, c->st));
+    dl_solve_params sp;
+    sp.tol = tol;
+    sp.max_iter = max_iter;
+    sp.prec_hi = hi;
+    sp.prec_lo = prm->prec_lo;
+    sp.delta = delta;
+    sp.flavour = 1;
+    sp.chunk = 0;
+    dl_status rs = solve_internal(c, B, sp, ee, eo, xe, po, false, nullptr);
+    if (rs < 0) return rs;
+    if (nc) *nc = rs == DL_NOT_CONVERGED;
+    fe[0] = ee;
+    fe[1] = eo;
+    fe[2] = xe;
+    fe[3] = po;
+    return DL_OK;
+  };
+  // right-hand-side tile: given, or the fastest per column-iteration of a short timed run
+  int tile = prm->tile;
+  if (tile == 0) {
+    double best = 1e300;
+    const int cand[3] = {8, 16, 32};
+    for (int ci = 0; ci < 3; ++ci) {
+      Batch B;
+      Field* fe[4];
+      if (!make_batch_multi(c, cand[ci], n, B)) continue;
+      if ((s = run(cand[ci], 2, 1e-300, 0.0, B, fe, nullptr)) != DL_OK) return s;  // capture the graph
+      CK(cudaStreamSynchronize(c->st));
+      auto a0 = std::chrono::steady_clock::now();
+      if ((s = run(cand[ci], 6, 1e-300, 0.0, B, fe, nullptr)) != DL_OK) return s;
+      CK(cudaStreamSynchronize(c->st));
+      const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - a0).count();
+      if (dt < best) {
+        best = dt;
+        tile = cand[ci];
+      }
+    }
+    if (tile == 0) return fail(c, DL_ERR_ARG, "dl_batch_loops: no tile fits");
+  }
+  auto t1 = std::chrono::steady_clock::now();
+  Batch B;
+  Field* fe[4];
+  bool nc = false;
+  if ((s = run(tile, prm->max_iter, prm->tol, prm->delta, B, fe, &nc)) != DL_OK) return s;
+  CK(cudaStreamSynchronize(c->st));
+  auto t2 = std::chrono::steady_clock::now();
+  // loops at p = 0 per lattice: [2 estimators][n][T_l][4][4]
+  if ((s = ensure_momenta(c, 0)) != DL_OK) return s;
+  size_t total = 0;
+  std::vector<size_t> loff(nl), soff(nl);
+  size_t so = 0;
+  for (int l = 0; l < nl; ++l) {
+    loff[l] = total;
+    total += (size_t)2 * n * c->lats[l].dims[3] * 16;
+    soff[l] = so;
+    so += (size_t)n * 2 * c->lats[l].Vh * 12;
+  }
+  void* p;
+  if ((s = ensure_buf(c, "bt_loops", sizeof(double2) * total, &p)) != DL_OK) return s;
+  double2* dloops = (double2*)p;
+  int inst = 0;
+  for (int l = 0; l < nl; ++l)
+    for (int k = 0; k * tile < n; ++k, ++inst) {
+      Batch B1;
+      memset(&B1, 0, sizeof(B1));
+      B1.nlat = 1;
+      B1.lat[0] = B.lat[inst];
+      B1.pstride = B.pstride;
+      dl::blocks_for(B1, 256);
+      const int T = B1.lat[0].T;
+      double2* o1 = dloops + loff[l] + ((size_t)0 * n + (size_t)k * tile) * T * 16;
+      double2* o2 = dloops + loff[l] + ((size_t)1 * n + (size_t)k * tile) * T * 16;
+      const double pim = -4.0 * B1.lat[0].kappa * B1.lat[0].amu;
+      if ((s = contract_internal(c, B1, hi, DL_EST_ONE_END, 0, 0, fe[2], fe[3], fe[0], fe[1], 0.0, pim, o1, 0)) != DL_OK)
+        return s;
+      if ((s = contract_internal(c, B1, hi, DL_EST_GEN, 0, 0, fe[2], fe[3], fe[0], fe[1], 2.0, 0.0, o2, 0)) != DL_OK)
+        return s;
+      if (sol) {
+        double2* sl = (double2*)sol + soff[l] + (size_t)k * tile * 2 * B1.lat[0].Vh * 12;
+        CK(dl::unpack(B1, hi, 0, sl, fe[2]->ref(), DL_C128, c->st));
+        CK(dl::unpack(B1, hi, 1, sl, fe[3]->ref(), DL_C128, c->st));
+      }
+    }
+  if (loops) CK(cudaMemcpyAsync(loops, dloops, sizeof(double2) * total, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  auto t3 = std::chrono::steady_clock::now();
+  inf.tile = tile;
+  inf.instances = B.nlat;
+  inf.seconds_tune = std::chrono::duration<double>(t1 - t0).count();
+  inf.seconds_solve = std::chrono::duration<double>(t2 - t1).count();
+  inf.seconds_contract = std::chrono::duration<double>(t3 - t2).count();
+  inf.not_converged = nc ? 1 : 0;
+  for (int l = 0; l < nl && l < DL_MAX_LAT; ++l) {
+    int mx = 0;
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int gc = l * n + i;  // instances of a lattice are consecutive, columns in order
+      if (gc < (int)c->last_iters.size()) mx = std::max(mx, c->last_iters[gc]);
+      if (gc < (int)c->last_resid.size()) rmax = std::max(rmax, c->last_resid[gc]);
+    }
+    inf.iters_max[l] = mx;
+    inf.resid_max[l] = rmax;
+  }
+  if (info) *info = inf;
+  if ((s = leave(c)) != DL_OK) return s;
+  return nc ? fail(c, DL_NOT_CONVERGED, "dl_batch_loops: a solve hit max_iter") : DL_OK;
 }
 
 }  // extern "C"
@@ -1370,13 +1588,13 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
     case DL_OP_M:
     case DL_OP_MDAG: {
       const bool dag = op == DL_OP_MDAG;
-      EpiSet E = epi(c, -c->kappa, 0, 0, 1, dag ? -f : f);
+      EpiSet E = epiB(B, CK_MK, 0, 0, 1, dag ? -f : f);
       CK(D(EPI_AUX, dag, 0, io, ie, oe, E));
       CK(D(EPI_AUX, dag, 1, ie, io, oo, E));
       break;
     }
     case DL_OP_HOP: {
-      EpiSet E = epi(c, 1.0, 0, 0, 0, 0);
+      EpiSet E = epiB(B, CK_ONE, 0, 0, 0, 0);
       CK(D(EPI_PLAIN, false, 0, io, NOF, oe, E));
       CK(D(EPI_PLAIN, false, 1, ie, NOF, oo, E));
       break;
@@ -1390,21 +1608,21 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
       break;
     }
     case DL_OP_PREP: {
-      EpiSet Ei = epi(c, 1.0, 2, f, 0, 0);
+      EpiSet Ei = epiB(B, CK_ONE, 2, f, 0, 0);
       CK(dl::twist(B, prec, t, io, Ei, nullptr, c->st));
-      EpiSet E = epi(c, c->kappa, 0, 0, 0, 0);
+      EpiSet E = epiB(B, CK_K, 0, 0, 0, 0);
       CK(D(EPI_AUX, false, 0, t, ie, oe, E));
       CK(dl::zero(B, prec, oo, nullptr, c->st));
       break;
     }
     case DL_OP_RECON: {
       CK(dl::copy(B, prec, prec, oe, ie, nullptr, c->st));
-      EpiSet E = epi(c, c->kappa, 2, f, 0, 0);
+      EpiSet E = epiB(B, CK_K, 2, f, 0, 0);
       CK(D(EPI_AUX, false, 1, ie, ao, oo, E));
       break;
     }
     case DL_OP_BH: {
-      EpiSet E = epi(c, -c->kappa, 2, f, 0, 0);
+      EpiSet E = epiB(B, CK_MK, 2, f, 0, 0);
       CK(D(EPI_PLAIN, false, 0, io, NOF, oe, E));
       CK(D(EPI_PLAIN, false, 1, ie, NOF, oo, E));
       break;

@@ -2,6 +2,8 @@
 // twist) and the per-column CG scalar kernels.  All reductions are per column
 // and deterministic: block partial sums in fixed order, then one CTA per
 // column sums the partials of its lattice's blocks in fixed order.
+#include <algorithm>
+
 #include "dl_internal.cuh"
 #include "dl_kernels.h"
 
@@ -53,7 +55,7 @@ __global__ void accum_kernel(Batch B, FieldRef x, FieldRef y, const int* mask, i
 template <int P>
 __global__ void xmy_norm_kernel(Batch B, FieldRef r, FieldRef b, FieldRef a, const int* mask, double* partial) {
   ITEM_PROLOGUE
-  double red = 0.0;
+  typename SIO<P>::real red = 0;  // per site-column in the storage arithmetic, FP64 across sites
   if (act) {
     typename SIO<P>::real bv[24], av[24];
     SIO<P>::load(seg_ptr<P>(b, L), seg_norm(b, L), nitems, j, bv);
@@ -61,25 +63,25 @@ __global__ void xmy_norm_kernel(Batch B, FieldRef r, FieldRef b, FieldRef a, con
 #pragma unroll
     for (int m = 0; m < 24; ++m) {
       bv[m] -= av[m];
-      red += (double)bv[m] * (double)bv[m];
+      red += bv[m] * bv[m];
     }
     SIO<P>::store(seg_ptr_w<P>(r, L), seg_norm(r, L), nitems, j, bv);
   }
-  block_reduce_cols(red, npad, partial, B.pstride);
+  block_reduce_cols((double)red, npad, partial, B.pstride);
 }
 
 // partial |v|^2 per column
 template <int P>
 __global__ void norm_kernel(Batch B, FieldRef v, const int* mask, double* partial) {
   ITEM_PROLOGUE
-  double red = 0.0;
+  typename SIO<P>::real red = 0;  // per site-column in the storage arithmetic, FP64 across sites
   if (act) {
     typename SIO<P>::real a[24];
     SIO<P>::load(seg_ptr<P>(v, L), seg_norm(v, L), nitems, j, a);
 #pragma unroll
-    for (int m = 0; m < 24; ++m) red += (double)a[m] * (double)a[m];
+    for (int m = 0; m < 24; ++m) red += a[m] * a[m];
   }
-  block_reduce_cols(red, npad, partial, B.pstride);
+  block_reduce_cols((double)red, npad, partial, B.pstride);
 }
 
 // p = r + beta p
@@ -105,7 +107,7 @@ __global__ void twist_kernel(Batch B, FieldRef out, FieldRef in, EpiSet ep, cons
   typedef typename SIO<P>::real R;
   R v[24];
   SIO<P>::load(seg_ptr<P>(in, L), seg_norm(in, L), nitems, j, v);
-  twist_apply<R>(v, (R)ep.e[l].a1, (R)ep.e[l].b1);
+  twist_apply<R>(v, epc<R>(ep.e[l].a1, ep.e[l].a1f), epc<R>(ep.e[l].b1, ep.e[l].b1f));
   SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, v);
 }
 
@@ -189,7 +191,7 @@ __global__ void cg_beta_kernel(int ncols, double* S, int* active, int* flags, in
 // one, or one has waited 16 iterations, so that updates are done in batches
 // (each update applies the high-precision operator to every waiting column).
 __global__ void cg_cond_kernel(int ncols, const int* __restrict__ active, const int* __restrict__ flags, int* counter,
-                               const int* limit, int* wait, cudaGraphConditionalHandle h) {
+                               const int* limit, int* wait, cudaGraphConditionalHandle h, int* cont) {
   const int gc = threadIdx.x;
   const int a = (gc < ncols) && active[gc] != 0;
   const int u = a && (flags[gc] & DL_FLAG_UPDATE) != 0;
@@ -205,18 +207,137 @@ __global__ void cg_cond_kernel(int ncols, const int* __restrict__ active, const 
     const int n = *counter + 1;
     *counter = n;
     const bool due = n_u > 0 && (2 * n_u >= n_a || old);
-    cudaGraphSetConditional(h, (n_a > 0 && !due && n < *limit) ? 1u : 0u);
+    const unsigned go = (n_a > 0 && !due && n < *limit) ? 1u : 0u;
+    if (cont)
+      *cont = (int)go;  // launched outside a graph: the host reads the decision
+    else
+      cudaGraphSetConditional(h, go);
   }
+}
+
+// <a, b> = sum conj(a) b over both parities of one column (single-column batch):
+// grid-stride CTAs write partial[blk] (re) and partial[pstride + blk] (im); a
+// second one-CTA kernel adds them in a fixed order.
+template <int P>
+__global__ void pdot_kernel(Batch B, FieldRef ae, FieldRef ao, FieldRef be, FieldRef bo, double* partial) {
+  const LatDesc& L = B.lat[0];
+  const long long nitems = (long long)L.Vh << L.lognpad;
+  double re = 0.0, im = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * nitems; q += (long long)gridDim.x * blockDim.x) {
+    const bool odd = q >= nitems;
+    const long long j = odd ? q - nitems : q;
+    if ((int)(j & ((1 << L.lognpad) - 1)) >= L.ncol) continue;
+    typedef typename SIO<P>::real R;
+    R av[24], bv[24];
+    const FieldRef& a = odd ? ao : ae;
+    const FieldRef& b = odd ? bo : be;
+    SIO<P>::load(seg_ptr<P>(a, L), seg_norm(a, L), nitems, j, av);
+    SIO<P>::load(seg_ptr<P>(b, L), seg_norm(b, L), nitems, j, bv);
+    R sr = 0, si = 0;  // one site in the storage arithmetic, FP64 across sites
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      sr += av[2 * m] * bv[2 * m] + av[2 * m + 1] * bv[2 * m + 1];
+      si += av[2 * m] * bv[2 * m + 1] - av[2 * m + 1] * bv[2 * m];
+    }
+    re += (double)sr;
+    im += (double)si;
+  }
+  __shared__ double sr[32], si[32];
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += sr[w];
+      ti += si[w];
+    }
+    partial[blockIdx.x] = tr;
+    partial[(size_t)B.pstride + blockIdx.x] = ti;
+  }
+}
+
+__global__ void pdot_final_kernel(const double* __restrict__ partial, int nblk, int pstride, double* out) {
+  __shared__ double sr[256], si[256];
+  double re = 0.0, im = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    re += partial[b];
+    im += partial[(size_t)pstride + b];
+  }
+  sr[threadIdx.x] = re;
+  si[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sr[threadIdx.x] += sr[threadIdx.x + w];
+      si[threadIdx.x] += si[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sr[0];
+    out[1] = si[0];
+  }
+}
+
+template <int P>
+__global__ void caxpy_kernel(Batch B, double ar, double ai, FieldRef x, FieldRef y) {
+  const LatDesc& L = B.lat[0];
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nitems = (long long)L.Vh << L.lognpad;
+  if (j >= nitems || (int)(j & ((1 << L.lognpad) - 1)) >= L.ncol) return;
+  typedef typename SIO<P>::real R;
+  R xv[24], yv[24];
+  SIO<P>::load(seg_ptr<P>(x, L), seg_norm(x, L), nitems, j, xv);
+  SIO<P>::load(seg_ptr<P>(y, L), seg_norm(y, L), nitems, j, yv);
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    const R xr = xv[2 * m], xi = xv[2 * m + 1];
+    yv[2 * m] += (R)ar * xr - (R)ai * xi;
+    yv[2 * m + 1] += (R)ar * xi + (R)ai * xr;
+  }
+  SIO<P>::store(seg_ptr_w<P>(y, L), seg_norm(y, L), nitems, j, yv);
 }
 
 }  // namespace
 
 namespace dl {
 
-cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter, const int* limit, int* wait,
-                    cudaGraphConditionalHandle h, cudaStream_t st) {
+cudaError_t pdot(const Batch& B, int prec, FieldRef ae, FieldRef ao, FieldRef be, FieldRef bo, double* partial,
+                 double* out, cudaStream_t st) {
+  const long long items = (long long)B.lat[0].Vh << B.lat[0].lognpad;
+  const int g = (int)std::min<long long>((2 * items + 255) / 256, std::min<long long>(4 * 152, B.pstride));
+  if (g < 1) return cudaErrorInvalidValue;
   DL_COUNT();
-  cg_cond_kernel<<<1, DL_NCMAX, 0, st>>>(ncols, active, flags, counter, limit, wait, h);
+  if (prec == P64) pdot_kernel<P64><<<g, 256, 0, st>>>(B, ae, ao, be, bo, partial);
+  else if (prec == P32) pdot_kernel<P32><<<g, 256, 0, st>>>(B, ae, ao, be, bo, partial);
+  else return cudaErrorInvalidValue;
+  DL_COUNT();
+  pdot_final_kernel<<<1, 256, 0, st>>>(partial, g, B.pstride, out);
+  return cudaGetLastError();
+}
+
+cudaError_t caxpy(const Batch& Bin, int prec, double ar, double ai, FieldRef x, FieldRef y, cudaStream_t st) {
+  Batch B = Bin;
+  const int g = blocks_for(B, 256);
+  if (!g) return cudaSuccess;
+  DL_COUNT();
+  if (prec == P64) caxpy_kernel<P64><<<g, 256, 0, st>>>(B, ar, ai, x, y);
+  else if (prec == P32) caxpy_kernel<P32><<<g, 256, 0, st>>>(B, ar, ai, x, y);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter, const int* limit, int* wait,
+                    cudaGraphConditionalHandle h, int* cont, cudaStream_t st) {
+  DL_COUNT();
+  cg_cond_kernel<<<1, DL_NCMAX, 0, st>>>(ncols, active, flags, counter, limit, wait, h, cont);
   return cudaGetLastError();
 }
 
@@ -227,6 +348,7 @@ static int grid_of(Batch& B) { return blocks_for(B, 256); }
     case P64: { constexpr int PP = P64; CALL; } break; \
     case P32: { constexpr int PP = P32; CALL; } break; \
     case P16: { constexpr int PP = P16; CALL; } break; \
+    case PBF: { constexpr int PP = PBF; CALL; } break; \
     default: return cudaErrorInvalidValue; \
   }
 
@@ -236,6 +358,7 @@ cudaError_t copy(const Batch& Bin, int pd, int ps, FieldRef dst, FieldRef src, c
   if (!g) return cudaSuccess;
 #define CP(a, b) if (pd == a && ps == b) { DL_COUNT(); copy_kernel<a, b><<<g, 256, 0, st>>>(B, dst, src, mask); return cudaGetLastError(); }
   CP(P64, P64) CP(P64, P32) CP(P64, P16) CP(P32, P64) CP(P32, P32) CP(P32, P16) CP(P16, P64) CP(P16, P32) CP(P16, P16)
+  CP(PBF, P64) CP(P64, PBF) CP(PBF, P32) CP(P32, PBF)
 #undef CP
   return cudaErrorInvalidValue;
 }

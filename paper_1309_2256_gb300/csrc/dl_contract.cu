@@ -16,38 +16,43 @@ namespace {
 
 enum { MODE_STANDARD = 0, MODE_ONE_END = 1, MODE_GEN = 2, MODE_HPE = 3 };
 
-template <int P>
-__device__ __forceinline__ void load_d(const FieldRef& f, const LatDesc& L, long long nitems, long long j, double v[24]) {
+template <int P, typename R>
+__device__ __forceinline__ void load_r(const FieldRef& f, const LatDesc& L, long long nitems, long long j, R v[24]) {
   typename SIO<P>::real a[24];
   SIO<P>::load(seg_ptr<P>(f, L), seg_norm(f, L), nitems, j, a);
 #pragma unroll
-  for (int m = 0; m < 24; ++m) v[m] = (double)a[m];
+  for (int m = 0; m < 24; ++m) v[m] = (R)a[m];
 }
 
-// (xi, phi) of an estimator at one site from s (or w) and eta.
-template <int P, int MODE>
+// (xi, phi) of an estimator at one site from s (or w) and eta, in the
+// arithmetic type R (FP32 for the low-precision pipeline: no FP64 instructions).
+template <int P, int MODE, typename R>
 __device__ __forceinline__ void make_pair(const FieldRef& s, const FieldRef& eta, const LatDesc& L, long long nitems,
-                                          long long j, double xi[24], double phi[24]) {
+                                          long long j, R xi[24], R phi[24]) {
   if (MODE == MODE_STANDARD || MODE == MODE_HPE) {
-    load_d<P>(eta, L, nitems, j, xi);
-    load_d<P>(s, L, nitems, j, phi);
+    load_r<P, R>(eta, L, nitems, j, xi);
+    load_r<P, R>(s, L, nitems, j, phi);
   } else if (MODE == MODE_ONE_END) {
-    load_d<P>(s, L, nitems, j, phi);
+    load_r<P, R>(s, L, nitems, j, phi);
 #pragma unroll
     for (int m = 0; m < 24; ++m) xi[m] = (m < 12) ? phi[m] : -phi[m];
   } else {  // generalised: xi = g5 s, phi = g5 eta - 2 i kappa amu s
-    double e[24];
-    load_d<P>(s, L, nitems, j, xi);
-    load_d<P>(eta, L, nitems, j, e);
-    const double k2 = 2.0 * L.kappa * L.amu;
+    R e[24];
+    load_r<P, R>(s, L, nitems, j, xi);
+    load_r<P, R>(eta, L, nitems, j, e);
+    const R k2 = (R)(2.0 * L.kappa * L.amu);
 #pragma unroll
     for (int m = 0; m < 12; ++m) {
-      double g = (m < 6) ? 1.0 : -1.0;
-      double sr = xi[2 * m], si = xi[2 * m + 1];
-      phi[2 * m] = g * e[2 * m] + k2 * si;
-      phi[2 * m + 1] = g * e[2 * m + 1] - k2 * sr;
-      xi[2 * m] = g * sr;
-      xi[2 * m + 1] = g * si;
+      const R sr = xi[2 * m], si = xi[2 * m + 1];
+      if (m < 6) {
+        phi[2 * m] = e[2 * m] + k2 * si;
+        phi[2 * m + 1] = e[2 * m + 1] - k2 * sr;
+      } else {
+        phi[2 * m] = -e[2 * m] + k2 * si;
+        phi[2 * m + 1] = -e[2 * m + 1] - k2 * sr;
+        xi[2 * m] = -sr;
+        xi[2 * m + 1] = -si;
+      }
     }
   }
 }
@@ -76,7 +81,7 @@ __global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, Field
   const int p = (x + y + z + t) & 1;
   const long long jj = ((long long)(lex >> 1) << L.lognpad) + col;
   double xi[24], phi[24];
-  make_pair<P, MODE>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, jj, xi, phi);
+  make_pair<P, MODE, double>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, jj, xi, phi);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -105,7 +110,7 @@ __global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, Field
       const int lexn = lex_of(L, xn, yn, zn, tn);
       const long long jn = ((long long)(lexn >> 1) << L.lognpad) + col;
       double xif[24], phif[24];
-      make_pair<P, MODE>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, jn, xif, phif);
+      make_pair<P, MODE, double>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, jn, xif, phif);
 #pragma unroll
       for (int m = 0; m < 24; ++m) {
         xif[m] *= bc;
@@ -113,7 +118,7 @@ __global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, Field
       }
       // U_mu(x), parity p, checkerboard index lex >> 1
       double u[18];
-      const double2* gl = g64 + (size_t)((p * 4 + mu) * 9) * L.Vh + (lex >> 1);
+      const double2* gl = (const double2*)gauge_seg<G64R18>(g64, L) + (size_t)((p * 4 + mu) * 9) * L.Vh + (lex >> 1);
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         double2 c = gl[(size_t)k * L.Vh];
@@ -168,18 +173,26 @@ __global__ void contract_sites_kernel(Batch B, FieldRef s_e, FieldRef s_o, Field
 // Fused per-site bilinears and x-direction DFT.  One CTA per (t, z, y) row;
 // thread (x, column) forms the 16 (per derivative slot) components of its site
 // in R, stores them to shared memory, and the CTA then writes
-//   G1[comp][t][z][y][nx][col] = sum_x exp(-2 pi i nx x / X) C_comp(x, col).
-// Derivative slots d = 1..4 (mu = d - 1) are processed one at a time.
-template <int P, int MODE, bool DERIV, typename R>
+//   G1[comp][t][z][y][nx][col] = sum_x exp(-2 pi i nx x / X) C_comp(x, col)
+// as R pairs.  Derivative slots d = 1..4 (mu = d - 1) are processed one at a
+// time; their links come from the gauge copy G of the same precision as R
+// (FP64 recon-18 for R = double, the FP32 copy otherwise), so the FP32 pipeline
+// issues no FP64 instructions.
+template <typename R>
+struct RPair {
+  R x, y;
+};
+
+template <int P, int MODE, bool DERIV, typename R, int G>
 __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
-                                                           FieldRef eta_o, const double2* __restrict__ g64, int mx,
-                                                           int cwlog, double2* __restrict__ G1) {
+                                                           FieldRef eta_o, const void* __restrict__ gbase, int mx,
+                                                           int cwlog, RPair<R>* __restrict__ G1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const LatDesc& L = B.lat[0];
   const int lg = L.lognpad, npad = 1 << lg;
   const int cw = 1 << cwlog;                     // columns handled by this CTA
   const int NX = 2 * mx + 1;
-  typedef struct { R x, y; } cr;
+  typedef RPair<R> cr;
   cr* cs = (cr*)smem_raw;                        // [16][X][cw]
   cr* ph = cs + 16 * L.X * cw;                   // [X]
   const int row = blockIdx.x;                    // (t * Z + z) * Y + y
@@ -196,8 +209,8 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
   const int lex = lex_of(L, x, y, z, t);
   const int p = (x + y + z + t) & 1;
   const bool live = col < L.ncol;
-  double xi[24], phi[24];
-  if (live) make_pair<P, MODE>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, ((long long)(lex >> 1) << lg) + col, xi, phi);
+  R xi[24], phi[24];
+  if (live) make_pair<P, MODE, R>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, ((long long)(lex >> 1) << lg) + col, xi, phi);
   const long long nrows = (long long)L.T * L.Z * L.Y;
   const int nd = DERIV ? 5 : 1;
   for (int d = 0; d < nd; ++d) {
@@ -213,8 +226,8 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
             R re = 0, im = 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              R xr = (R)xi[2 * (3 * a + c)], xim = (R)xi[2 * (3 * a + c) + 1];
-              R pr = (R)phi[2 * (3 * b + c)], pim = (R)phi[2 * (3 * b + c) + 1];
+              const R xr = xi[2 * (3 * a + c)], xim = xi[2 * (3 * a + c) + 1];
+              const R pr = phi[2 * (3 * b + c)], pim = phi[2 * (3 * b + c) + 1];
               re += xr * pr + xim * pim;
               im += xr * pim - xim * pr;
             }
@@ -224,25 +237,19 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
       } else {
         const int mu = d - 1;
         int xn = x, yn = y, zn = z, tn = t;
-        double bc = 1.0;
+        R bc = 1;
         if (mu == 0) xn = (x + 1 == L.X) ? 0 : x + 1;
         if (mu == 1) yn = (y + 1 == L.Y) ? 0 : y + 1;
         if (mu == 2) zn = (z + 1 == L.Z) ? 0 : z + 1;
         if (mu == 3) {
           tn = (t + 1 == L.T) ? 0 : t + 1;
-          if (t + 1 == L.T) bc = L.tbc;
+          if (t + 1 == L.T) bc = (R)L.tbc;
         }
         const int lexn = lex_of(L, xn, yn, zn, tn);
-        double xif[24], phif[24];
-        make_pair<P, MODE>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, ((long long)(lexn >> 1) << lg) + col, xif, phif);
-        double u[18];
-        const double2* gl = g64 + (size_t)((p * 4 + mu) * 9) * L.Vh + (lex >> 1);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          double2 cc = gl[(size_t)k * L.Vh];
-          u[2 * k] = cc.x;
-          u[2 * k + 1] = cc.y;
-        }
+        R xif[24], phif[24];
+        make_pair<P, MODE, R>(p ? s_e : s_o, p ? eta_e : eta_o, L, nitems, ((long long)(lexn >> 1) << lg) + col, xif, phif);
+        R u[18];
+        GIO<G>::load(gauge_seg<G>(gbase, L), L.Vh, p, mu, lex >> 1, u);
         R up[24], udp[24];
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
@@ -251,12 +258,12 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
             R r1 = 0, i1 = 0, r2 = 0, i2 = 0;
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-              R ur = (R)u[2 * (3 * a + b)], ui = (R)u[2 * (3 * a + b) + 1];
-              R vr = (R)(phif[2 * (3 * sp + b)] * bc), vi = (R)(phif[2 * (3 * sp + b) + 1] * bc);
+              const R ur = u[2 * (3 * a + b)], ui = u[2 * (3 * a + b) + 1];
+              const R vr = phif[2 * (3 * sp + b)] * bc, vi = phif[2 * (3 * sp + b) + 1] * bc;
               r1 += ur * vr - ui * vi;
               i1 += ur * vi + ui * vr;
-              R wr = (R)u[2 * (3 * b + a)], wi = -(R)u[2 * (3 * b + a) + 1];
-              R qr = (R)phi[2 * (3 * sp + b)], qi = (R)phi[2 * (3 * sp + b) + 1];
+              const R wr = u[2 * (3 * b + a)], wi = -u[2 * (3 * b + a) + 1];
+              const R qr = phi[2 * (3 * sp + b)], qi = phi[2 * (3 * sp + b) + 1];
               r2 += wr * qr - wi * qi;
               i2 += wr * qi + wi * qr;
             }
@@ -272,12 +279,12 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
             R re = 0, im = 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-              R xr = (R)xi[2 * (3 * a + c)], xim = (R)xi[2 * (3 * a + c) + 1];
-              R pr = up[2 * (3 * b + c)], pim = up[2 * (3 * b + c) + 1];
+              const R xr = xi[2 * (3 * a + c)], xim = xi[2 * (3 * a + c) + 1];
+              const R pr = up[2 * (3 * b + c)], pim = up[2 * (3 * b + c) + 1];
               re += xr * pr + xim * pim;
               im += xr * pim - xim * pr;
-              R fr = (R)(xif[2 * (3 * a + c)] * bc), fim = (R)(xif[2 * (3 * a + c) + 1] * bc);
-              R qr = udp[2 * (3 * b + c)], qim = udp[2 * (3 * b + c) + 1];
+              const R fr = xif[2 * (3 * a + c)] * bc, fim = xif[2 * (3 * a + c) + 1] * bc;
+              const R qr = udp[2 * (3 * b + c)], qim = udp[2 * (3 * b + c) + 1];
               re -= fr * qr + fim * qim;
               im -= fr * qim - fim * qr;
             }
@@ -310,8 +317,7 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
         q += n;
         if (q >= L.X) q -= L.X;
       }
-      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] =
-          make_double2((double)re, (double)im);
+      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] = cr{re, im};
     }
   }
 }
@@ -330,10 +336,10 @@ __global__ void phase_kernel(int len, double2* ph) {
 // (2m+1) x tile outputs from shared memory.
 #define DL_DFT_TILE 64
 template <typename R>
-__global__ void __launch_bounds__(256) dft_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long nb,
+__global__ void __launch_bounds__(256) dft_kernel(const RPair<R>* __restrict__ in, RPair<R>* __restrict__ out, long long nb,
                                                   int len, long long stride, int m, const double2* __restrict__ ph) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  typedef struct { R x, y; } cr;
+  typedef RPair<R> cr;
   cr* slab = (cr*)smem_raw;            // [len][DL_DFT_TILE]
   cr* phs = slab + len * DL_DFT_TILE;  // [len]
   const long long ntile = (stride + DL_DFT_TILE - 1) / DL_DFT_TILE;
@@ -344,14 +350,10 @@ __global__ void __launch_bounds__(256) dft_kernel(const double2* __restrict__ in
     phs[q].x = (R)ph[q].x;
     phs[q].y = (R)ph[q].y;
   }
-  const double2* src = in + b * len * stride + s0;
+  const cr* src = in + b * len * stride + s0;
   for (int e = threadIdx.x; e < len * DL_DFT_TILE; e += blockDim.x) {
     const int j = e / DL_DFT_TILE, ss = e % DL_DFT_TILE;
-    if (ss < tw) {
-      const double2 v = src[(long long)j * stride + ss];
-      slab[e].x = (R)v.x;
-      slab[e].y = (R)v.y;
-    }
+    if (ss < tw) slab[e] = src[(long long)j * stride + ss];
   }
   __syncthreads();
   const int nk = 2 * m + 1;
@@ -371,13 +373,14 @@ __global__ void __launch_bounds__(256) dft_kernel(const double2* __restrict__ in
       q += n;
       if (q >= len) q -= len;
     }
-    out[(b * nk + k) * stride + s0 + ss] = make_double2((double)re, (double)im);
+    out[(b * nk + k) * stride + s0 + ss] = cr{re, im};
   }
 }
 
-// out[col][t][ip][d][ab] (+)= pre * finalised G3
+// out[col][t][ip][d][ab] (+)= pre * finalised G3 (G3 holds R pairs)
+template <typename R>
 __global__ void finalize_kernel(LatDesc L, int npad, int nd, int np, const int* __restrict__ mom, int mx, int my, int mz,
-                                const double2* __restrict__ G3,
+                                const RPair<R>* __restrict__ G3,
                                 double pre_re, double pre_im, double2* out, int accumulate) {
   const long long tot = (long long)L.ncol * L.T * np * nd * 16;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -395,7 +398,7 @@ __global__ void finalize_kernel(LatDesc L, int npad, int nd, int np, const int* 
   const long long cube = (long long)NZ * NY * NX * npad;
   auto g = [&](int comp, int tt) -> double2 {
     long long o = ((long long)comp * L.T + tt) * cube + (((long long)(nz + mz) * NY + (ny + my)) * NX + (nx + mx)) * npad + col;
-    return G3[o];
+    return make_double2((double)G3[o].x, (double)G3[o].y);
   };
   double2 v;
   if (d == 0) {
@@ -605,32 +608,39 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
 }
 
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
-                       FieldRef eta_o, const void* g64, int mx, double2* G1, cudaStream_t st) {
+                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* G1,
+                       cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   const int npad = 1 << L.lognpad;
   int cwlog = L.lognpad;
   while (cwlog > 0 && (L.X << cwlog) > 256) --cwlog;  // X * cw <= 256 threads per CTA
   const int threads = L.X << cwlog;
   if (threads > 256 || threads < 1) return cudaErrorInvalidValue;
+  if (prec != P64 && rec32 != 12 && rec32 != 8) return cudaErrorInvalidValue;
   const dim3 grid(L.T * L.Z * L.Y, npad >> cwlog);
-  const double2* gg = (const double2*)g64;
-#define CX(PR, MD, R)                                                                                              \
-  if (prec == PR && mode == MD) {                                                                                  \
+#define CXK(PR, MD, DV, R, G, GB)                                                                                   \
+  {                                                                                                                \
     const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + L.X) * 2 * sizeof(R);                                   \
-    if (with_deriv) {                                                                                              \
-      cudaFuncSetAttribute(contract_x_kernel<PR, MD, true, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
-      DL_COUNT();                                                                                                  \
-      contract_x_kernel<PR, MD, true, R><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gg, mx, cwlog, G1); \
-    } else {                                                                                                       \
-      cudaFuncSetAttribute(contract_x_kernel<PR, MD, false, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
-      DL_COUNT();                                                                                                  \
-      contract_x_kernel<PR, MD, false, R><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gg, mx, cwlog, G1); \
-    }                                                                                                              \
+    cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
+    DL_COUNT();                                                                                                    \
+    contract_x_kernel<PR, MD, DV, R, G><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, GB, mx, cwlog,      \
+                                                                      (RPair<R>*)G1);                              \
     return cudaGetLastError();                                                                                     \
   }
-  CX(P64, 0, double) CX(P64, 1, double) CX(P64, 2, double) CX(P64, 3, double)
-  CX(P32, 0, float) CX(P32, 1, float) CX(P32, 2, float) CX(P32, 3, float)
+#define CX(PR, MD)                                                                                                  \
+  if (prec == PR && mode == MD) {                                                                                  \
+    if (PR == P64) {                                                                                               \
+      if (with_deriv) CXK(PR, MD, true, double, G64R18, g64) else CXK(PR, MD, false, double, G64R18, g64)         \
+    } else if (rec32 == 12) {                                                                                      \
+      if (with_deriv) CXK(PR, MD, true, float, G32R12, g32) else CXK(PR, MD, false, float, G32R12, g32)           \
+    } else {                                                                                                       \
+      if (with_deriv) CXK(PR, MD, true, float, G32R8, g32) else CXK(PR, MD, false, float, G32R8, g32)             \
+    }                                                                                                              \
+  }
+  CX(P64, 0) CX(P64, 1) CX(P64, 2) CX(P64, 3)
+  CX(P32, 0) CX(P32, 1) CX(P32, 2) CX(P32, 3)
 #undef CX
+#undef CXK
   return cudaErrorInvalidValue;
 }
 
@@ -645,28 +655,35 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
   DL_COUNT();
   if ((size_t)(len * DL_DFT_TILE + len) * 2 * (fp32 ? sizeof(float) : sizeof(double)) > 200000)
     return cudaErrorInvalidValue;  // extents up to ~190 (FP64) / ~380 (FP32) sites
-  if (fp32) {
+  if (fp32) {  // in and out hold float pairs
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(float);
     cudaFuncSetAttribute(dft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
-    dft_kernel<float><<<(int)g, 256, smem, st>>>(in, out, nb, len, stride, m, phase);
+    dft_kernel<float><<<(int)g, 256, smem, st>>>((const RPair<float>*)in, (RPair<float>*)out, nb, len, stride, m, phase);
   } else {
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(double);
     cudaFuncSetAttribute(dft_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
-    dft_kernel<double><<<(int)g, 256, smem, st>>>(in, out, nb, len, stride, m, phase);
+    dft_kernel<double><<<(int)g, 256, smem, st>>>((const RPair<double>*)in, (RPair<double>*)out, nb, len, stride, m,
+                                                 phase);
   }
   return cudaGetLastError();
 }
 
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
-                              const double2* G3, double pre_re, double pre_im, double2* out, int accumulate,
+                              const double2* G3, int fp32, double pre_re, double pre_im, double2* out, int accumulate,
                               cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   int nd = with_deriv ? 5 : 1;
   long long tot = (long long)L.ncol * L.T * np * nd * 16;
   if (tot == 0) return cudaSuccess;
   DL_COUNT();
-  finalize_kernel<<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz, G3, pre_re,
-                                                           pre_im, out, accumulate);
+  if (fp32)
+    finalize_kernel<float><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
+                                                                    (const RPair<float>*)G3, pre_re, pre_im, out,
+                                                                    accumulate);
+  else
+    finalize_kernel<double><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
+                                                                     (const RPair<double>*)G3, pre_re, pre_im, out,
+                                                                     accumulate);
   return cudaGetLastError();
 }
 

@@ -21,14 +21,14 @@ template <int P, int EPI, typename R>
 __device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDesc& L, long long nitems, long long j,
                                            int col, const FieldRef& aux, const FieldRef& out, const FieldRef& cr,
                                            const FieldRef& cy, const FieldRef& cp, const double* alpha) {
-  double red = 0.0;
-  const R c = (R)e.c;
+  R red = 0;  // this site-column's |.|^2 in R; the sums over sites are FP64
+  const R c = epc<R>(e.c, e.cf);
 #pragma unroll
   for (int m = 0; m < 24; ++m) acc[m] *= c;
   R v[24];
   if (EPI != EPI_PLAIN) {
     SIO<P>::load(seg_ptr<P>(aux, L), seg_norm(aux, L), nitems, j, v);
-    twist_apply<R>(v, (R)e.a2, (R)e.b2);
+    twist_apply<R>(v, epc<R>(e.a2, e.a2f), epc<R>(e.b2, e.b2f));
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] += v[m];
   }
@@ -38,7 +38,7 @@ __device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDes
 #pragma unroll
     for (int m = 0; m < 24; ++m) {
       v[m] -= al * acc[m];
-      red += (double)v[m] * (double)v[m];
+      red += v[m] * v[m];
     }
     SIO<P>::store(seg_ptr_w<P>(cr, L), seg_norm(cr, L), nitems, j, v);
     SIO<P>::load(seg_ptr<P>(cp, L), seg_norm(cp, L), nitems, j, acc);  // p (Ap no longer needed)
@@ -47,14 +47,14 @@ __device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDes
     for (int m = 0; m < 24; ++m) v[m] += al * acc[m];
     SIO<P>::store(seg_ptr_w<P>(cy, L), seg_norm(cy, L), nitems, j, v);
   } else {
-    twist_apply<R>(acc, (R)e.a1, (R)e.b1);
+    twist_apply<R>(acc, epc<R>(e.a1, e.a1f), epc<R>(e.b1, e.b1f));
     if (EPI == EPI_AUX_NORM) {
 #pragma unroll
-      for (int m = 0; m < 24; ++m) red += (double)acc[m] * (double)acc[m];
+      for (int m = 0; m < 24; ++m) red += acc[m] * acc[m];
     }
     SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, acc);
   }
-  return red;
+  return (double)red;
 }
 
 // Neighbour of site (x,y,z,t) along direction d = 2 mu + (1 if backward): its

@@ -19,15 +19,16 @@
 // [blk_begin_l, blk_begin_{l+1}) and its own segment of every field.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
 
-#define DL_MAX_LAT 8
+#define DL_MAX_LAT 16
 #define DL_MAXC 32  // max columns (right-hand sides) per lattice segment
 
-enum { P64 = 0, P32 = 1, P16 = 2 };
+enum { P64 = 0, P32 = 1, P16 = 2, PBF = 3 };  // PBF: bfloat16 activations of the network
 
 // ---------------------------------------------------------------- batch
 struct LatDesc {
@@ -40,6 +41,7 @@ struct LatDesc {
   long long gsite_off;  // parity-site offset of this lattice in the gauge arrays
   double tbc;        // time-boundary factor
   double kappa, amu;
+  long long noise_base;  // noise index of column 0 (instances of one lattice differ)
 };
 
 struct Batch {
@@ -165,6 +167,37 @@ template <> struct SIO<P16> {
 #pragma unroll
       for (int q = 0; q < 4; ++q) w[q] = q_to_u16pair(v[8 * k + 2 * q] * sc, v[8 * k + 2 * q + 1] * sc);
       p[k * st + j] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+};
+
+// bfloat16 storage (network activations): 3 chunks of 8 bf16, no scale
+template <> struct SIO<PBF> {
+  typedef float real;
+  static constexpr int K = 3;
+  __device__ static __forceinline__ void load(const void* b, const float*, long long st, long long j, float v[24]) {
+    const uint4* p = (const uint4*)b;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c = __ldg(p + k * st + j);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 f = __bfloat1622float2(h[q]);
+        v[8 * k + 2 * q] = f.x;
+        v[8 * k + 2 * q + 1] = f.y;
+      }
+    }
+  }
+  __device__ static __forceinline__ void store(void* b, float*, long long st, long long j, const float v[24]) {
+    uint4* p = (uint4*)b;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c;
+      __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[8 * k + 2 * q], v[8 * k + 2 * q + 1]);
+      p[k * st + j] = c;
     }
   }
 };
@@ -437,7 +470,14 @@ struct DevBuf {
 //   out = T1 (c * D^{(dag)} in + T2 aux),  T = a + i b gamma_5
 struct Epi {
   double c, a1, b1, a2, b2;
+  float cf, a1f, b1f, a2f, b2f;  // the same coefficients rounded once to FP32 (FP32 and 16-bit kernels)
 };
+// An epilogue coefficient in the kernel's arithmetic type: GB300 issues FP64
+// (and FP64<->FP32 conversion) instructions at a small fraction of the FP32
+// rate, so the FP32 kernels read the pre-rounded copy.
+template <typename R> __device__ __forceinline__ R epc(double d, float f);
+template <> __device__ __forceinline__ double epc<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float epc<float>(double, float f) { return f; }
 struct EpiSet {
   Epi e[DL_MAX_LAT];
 };

@@ -33,8 +33,9 @@ cudaError_t sum_partials(const Batch& B, const double* partial, double* out, int
                          cudaStream_t st);
 cudaError_t cg_alpha(int ncols, double* S, int* active, int* flags, cudaStream_t st);
 cudaError_t cg_beta(int ncols, double* S, int* active, int* flags, int* iters, double tol2, double delta, cudaStream_t st);
+// Loop condition of the CG graph: sets h, or writes *cont when cont != nullptr (plain launches)
 cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter, const int* limit, int* wait,
-                    cudaGraphConditionalHandle h, cudaStream_t st);
+                    cudaGraphConditionalHandle h, int* cont, cudaStream_t st);
 
 // layout (single-lattice batches)
 cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void* natural, int dtype, cudaStream_t st);
@@ -49,10 +50,12 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
                            FieldRef eta_o, const void* g64, double2* W, cudaStream_t st);
 cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
                      int fp32, cudaStream_t st);
+// G1 (and the DFT passes' buffers) hold float pairs for prec != P64, double pairs for P64
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
-                       FieldRef eta_o, const void* g64, int mx, double2* G1, cudaStream_t st);
+                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* G1,
+                       cudaStream_t st);
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
-                              const double2* G3, double pre_re, double pre_im, double2* out, int accumulate,
+                              const double2* G3, int fp32, double pre_re, double pre_im, double2* out, int accumulate,
                               cudaStream_t st);
 cudaError_t hpe_exact(double kappa, double amu, int flavour, double2* out16, cudaStream_t st);
 cudaError_t add_exact_p0(const Batch& B, int np, int nd, int ip0, const double2* exact16, double scale, double2* out,
@@ -62,4 +65,24 @@ cudaError_t col_accumulate(const double2* blk, const double2* sub, int ncol, lon
 cudaError_t observables(const double2* l1, const double2* l2, int ncol, int T, int np, int nd, int ip0, double* obs,
                         cudaStream_t st);
 cudaError_t combine(const double2* x, const double2* y, double a, double b, long long n, double2* out, cudaStream_t st);
+// learned preconditioner (dl_network.cu)
+cudaError_t nn_forward(const LatDesc& L, int prec, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef y,
+                       const void* g32, const float2* W, int ci, int co, int lgin, int lgout, cudaStream_t st);
+cudaError_t nn_backward_x(const LatDesc& L, int prec, int grec, int parity, FieldRef ge, FieldRef go, FieldRef gx,
+                          const void* g32, const float2* W, int ci, int co, int lgin, int lgout, cudaStream_t st);
+cudaError_t nn_backward_w(const LatDesc& L, int prec, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef gp,
+                          const void* g32, int ci, int co, int lgin, int lgout, float2* partial, int slots,
+                          cudaStream_t st);
+cudaError_t nn_wsum(const float2* partial, int nslice, size_t nW, float2* grad, cudaStream_t st);
+cudaError_t nn_lossgrad(const Batch& B, int prec, FieldRef y, FieldRef s, FieldRef g, const double* inv_ns, double* partial,
+                        cudaStream_t st);
+cudaError_t nn_adam(float2* W, const float2* grad, float2* m, float2* v, size_t n, float lr, float b1, float b2, float eps,
+                    int step, float gscale, cudaStream_t st);
+// <a, b> over both parities of a single-column field, written to out[0] (re), out[1] (im) on the device
+cudaError_t pdot(const Batch& B, int prec, FieldRef ae, FieldRef ao, FieldRef be, FieldRef bo, double* partial,
+                 double* out, cudaStream_t st);
+cudaError_t copy_col(const LatDesc& L, int pd, int ps, FieldRef dst, int lgd, int cd, FieldRef src, int lgs, int cs,
+                     cudaStream_t st);
+// y += alpha x (single column, complex alpha)
+cudaError_t caxpy(const Batch& B, int prec, double ar, double ai, FieldRef x, FieldRef y, cudaStream_t st);
 }  // namespace dl

@@ -101,24 +101,25 @@ __global__ void noise_kernel(Batch B, int parity, FieldRef dst, unsigned long lo
     int x, y, z, t;
     cb_coords(L, i, parity, x, y, z, t);
     const unsigned long long V = 2ULL * (unsigned long long)L.Vh;
-    const unsigned long long r = first + (unsigned long long)col;
+    const unsigned long long r = first + (unsigned long long)L.noise_base + (unsigned long long)col;
     const unsigned long long n0 = (r * V + (unsigned long long)lex_of(L, x, y, z, t)) * 12ULL;
-    const double h = 1.0 / sqrt(2.0);
+    typedef typename SIO<P>::real R;
+    const R h = (R)(1.0 / sqrt(2.0));  // folded at compile time; entries are selected, not computed
 #pragma unroll
     for (int m = 0; m < 12; ++m) {
       unsigned long long w = splitmix64(seed, n0 + (unsigned long long)m);
       int b0 = (int)(w & 1ULL), b1 = (int)((w >> 1) & 1ULL);
-      double re, im;
+      R re, im;
       if (quadrant) {
         int qd = b0 + 2 * b1;
-        re = (qd == 0) ? 1.0 : (qd == 2 ? -1.0 : 0.0);
-        im = (qd == 1) ? 1.0 : (qd == 3 ? -1.0 : 0.0);
+        re = (qd == 0) ? (R)1 : (qd == 2 ? (R)-1 : (R)0);
+        im = (qd == 1) ? (R)1 : (qd == 3 ? (R)-1 : (R)0);
       } else {
-        re = (1.0 - 2.0 * b0) * h;
-        im = (1.0 - 2.0 * b1) * h;
+        re = b0 ? -h : h;
+        im = b1 ? -h : h;
       }
-      v[2 * m] = (typename SIO<P>::real)re;
-      v[2 * m + 1] = (typename SIO<P>::real)im;
+      v[2 * m] = re;
+      v[2 * m + 1] = im;
     }
   } else {
 #pragma unroll
@@ -193,6 +194,7 @@ namespace dl {
     case P64: { constexpr int PP = P64; CALL; } break; \
     case P32: { constexpr int PP = P32; CALL; } break; \
     case P16: { constexpr int PP = P16; CALL; } break; \
+    case PBF: { constexpr int PP = PBF; CALL; } break; \
     default: return cudaErrorInvalidValue; \
   }
 

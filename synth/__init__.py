@@ -137,6 +137,27 @@ def gaussian_spinors(dims, n: int, seed: int) -> np.ndarray:
     return ((g[:, 0] + 1j * g[:, 1]) / np.sqrt(2.0)).reshape(n, T, Z, Y, X, 4, 3)
 
 
+def network_weights(n_layers: int, channels: int, seed: int, scale: float = 0.05, identity: float = 1.0) -> np.ndarray:
+    """Initial weights of a parallel-transport network with channels 1 -> C -> ... -> C -> 1,
+    complex64 concatenated per layer in the [9 terms][4 spin factors][C_out][C_in] layout:
+    Gaussian entries of standard deviation scale / sqrt(36 C_in) per component, plus
+    `identity` on the local unit-spin term from input channel 0 to output channel 0
+    (the unused local spin factors 2, 3 stay zero)."""
+    out = []
+    cnt = 0
+    for l in range(n_layers):
+        ci = 1 if l == 0 else channels
+        co = 1 if l == n_layers - 1 else channels
+        n = 36 * co * ci
+        g = normals(seed, 2 * n, offset=cnt).reshape(n, 2)
+        cnt += 2 * n
+        w = ((g[:, 0] + 1j * g[:, 1]) * scale / np.sqrt(2.0 * 36 * ci)).reshape(9, 4, co, ci)
+        w[0, 2:] = 0.0
+        w[0, 0, 0, 0] += identity
+        out.append(w.ravel())
+    return np.concatenate(out).astype(np.complex64)
+
+
 # Configurations of the synthetic workloads: lattice (X, Y, Z, T), link
 # smearing eps, hopping parameter kappa, twisted mass a*mu.  Link seeds are
 # 1000 + id, noise seeds 2000 + id.
@@ -144,6 +165,7 @@ CONFIGS = {
     "tiny_4x4x4x4": dict(dims=(4, 4, 4, 4), eps=0.3, kappa=0.16, amu=0.01, id=0),
     "mixed_16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.4, kappa=0.161, amu=0.0055, id=1),
     "tsm_32x32x32x64": dict(dims=(32, 32, 32, 64), eps=0.4, kappa=0.1612, amu=0.0055, id=2),
+    "learned_16x16x16x32": dict(dims=(16, 16, 16, 32), eps=0.4, kappa=0.161, amu=0.0055, id=3),
 }
 
 
