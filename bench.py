@@ -175,7 +175,7 @@ def run_ours(args, rank, world, device):
         return dl.dl_tsm_params(n_hp=n_hp_s, n_lp=n_lp_s, tol_hp=TOL_HP, tol_lp=TOL_LP, prec_hp_lo=dl.DL_F32,
                                 prec_lp_lo=dl.DL_F16, delta_hp=args.delta_hp, block=BLOCK,
                                 seed=rank_seed(step, rank), p2max=P2MAX, with_deriv=0,
-                                hpe=1, max_iter=200000, chunk=32)
+                                hpe=1, max_iter=200000, chunk=32, hp_guess=1)
 
     loops = np.zeros((3, DIMS[3], npm, 1, 4, 4), dtype=np.complex128)
     obs = {"hp": [], "pair": [], "lp": []}
@@ -404,6 +404,10 @@ def learned_case(args):
     dl.dl_load_gauge(ctx, links, -1.0, 12, 8)
     dl.dl_set_params(ctx, kappa, amu)
     out = {"case": "learned_16x16x16x32", "data": "synthetic", "pairs": args.pairs, "fresh": args.fresh}
+    t_start = time.perf_counter()
+
+    def progress(what):
+        print(f"[learned {time.perf_counter() - t_start:8.1f} s] {what}", file=sys.stderr, flush=True)
     # training pairs from the plain solver (complex64 storage, FP64-accurate solutions)
     eta = torch.empty((args.pairs, V * 12), dtype=torch.complex64, device="cuda")
     sol = torch.empty_like(eta)
@@ -417,6 +421,7 @@ def learned_case(args):
         dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
     torch.cuda.synchronize()
     out["seconds_pairs"] = time.perf_counter() - t0
+    progress(f"{args.pairs} training pairs")
     nn = dl.dl_nn_create(ctx, 4, 16, dl.DL_BF16)
     dl.dl_nn_set_weights(nn, synth.network_weights(4, 16, 3000 + cfg["id"]))
     tp = dl.dl_nn_train_params(steps=args.train_steps, batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
@@ -425,6 +430,7 @@ def learned_case(args):
     hist = dl.dl_nn_train(nn, tp, args.pairs, eta, sol, dl.DL_C64)
     torch.cuda.synchronize()
     ttrain = time.perf_counter() - t0
+    progress(f"trained {args.train_steps} steps")
     k = max(1, min(20, len(hist) // 5))
     out["train"] = {"steps": args.train_steps, "batch": args.batch, "lr": args.lr, "seconds": ttrain,
                     "pair_passes_per_s": args.train_steps * args.batch / ttrain,
@@ -451,6 +457,7 @@ def learned_case(args):
         co = 1 if l == 3 else 16
         flops += V * (co * ci * 9 * 12 * 2 * 8 + ci * 8 * 4 * 3 * 3 * 8)
     out["apply"] = {"ms": ms_apply, "tflops": flops / ms_apply / 1e9, "flops_per_apply": flops}
+    progress(f"one application {ms_apply:.2f} ms")
     # fresh noise: FGCR with / without the network, plain mixed-precision CG
     fresh = torch.empty((args.fresh, V * 12), dtype=torch.complex128, device="cuda")
     for b in range(0, args.fresh, 32):
@@ -469,6 +476,7 @@ def learned_case(args):
             secs += stt.seconds
             ops += stt.op_applications
             nns += stt.nn_applications
+        progress(f"{name}: {n_fg} solves")
         out[name] = {"rhs": n_fg, "iters_mean": float(np.mean(its)), "true_resid_max": float(np.max(res)),
                      "seconds_per_rhs": secs / n_fg, "op_applications_per_rhs": ops / n_fg,
                      "nn_applications_per_rhs": nns / n_fg}
@@ -495,6 +503,7 @@ def learned_case(args):
         loops_ = np.zeros((2, dims[3], npm, 1, 4, 4), dtype=np.complex128)
         ohp, opr, olp = np.zeros((24, 4)), np.zeros((24, 4)), np.zeros((args.fresh, 4))
         st, info = dl.dl_tsm_run(ctx, prm, loops_, ohp, opr, olp)
+        progress(f"{name}: TSM")
         ee = _equal_error(ohp, opr, olp, 24, args.fresh, info.seconds_total)
         out[name] = {"seconds": info.seconds_total, "seconds_lp": info.seconds_lp,
                      "sigma_per_s": ee["sigma"]["per_s"], "axial_per_s": ee["axial"]["per_s"],
@@ -521,7 +530,7 @@ def batch_case(args):
     out = np.zeros(sum(2 * n * d[3] * 16 for d in dims), dtype=np.complex128)
     res = {"case": "batch_6_lattices", "data": "synthetic", "rhs_per_lattice": n}
     for rep in range(2):
-        prm = dl.dl_batch_params(n=n, tol=1e-8, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.1, seed=2004 + rep,
+        prm = dl.dl_batch_params(n=n, tol=1e-8, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.01, seed=2004 + rep,
                                  max_iter=20000, tile=0)
         st, info = dl.dl_batch_loops(ctx, prm, out, None)
     res.update({"tile": info.tile, "instances": info.instances, "seconds_tune": info.seconds_tune,
@@ -601,7 +610,7 @@ def main():
         "dtype": "f16/f32 Krylov, f64 reliable updates and accumulation",
         "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
-                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
+                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "hp_from_lp": 1, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
                    "step": "one TSM sweep: 24 HP-LP pairs + 500 LP solves + contractions",
                    "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -194,6 +194,9 @@ typedef struct {
                             map's output N(eta) stands in for every LP solution (on the
                             context's first-flavour operator); the HP correction of
                             Eq. estiTSM keeps the estimate unbiased for any map. */
+  int hp_guess;          /* 1: every HP solve starts from the LP solution of its noise
+                            vector (the HP tolerance is unchanged, so the HP solution is
+                            the same to that tolerance); 0: from zero */
 } dl_tsm_params;
 
 typedef struct {

@@ -434,7 +434,7 @@ dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F,
 // Solve Mhat^dag Mhat x = b (b: normal-equation rhs in hi precision) for n columns.
 // x (hi) receives the solution.  final_check recomputes the residual in hi.
 dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b, Field* x, bool final_check,
-                 dl_solve_stats* stats, double* resid_out) {
+                 dl_solve_stats* stats, double* resid_out, bool x_init) {
   const int hi = prm.prec_hi, lo = prm.prec_lo, f = prm.flavour;
   const int n = ncols_of(B);
   dl_status s;
@@ -448,24 +448,32 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
       (s = ensure_field(c, "cg_th1", hi, B, &F.th1)) || (s = ensure_field(c, "cg_tq", hi, B, &F.tq)) ||
       (s = ensure_field(c, "cg_th2", hi, B, &F.th2)))
     return s;
-  // x = 0, |b|^2
-  CK(dl::zero(B, hi, x->ref(), nullptr, c->st));
+  // |b|^2; x = 0 (r = b), or the caller's initial guess x (r = b - A x in the high precision)
   CK(dl::norm2(B, hi, b->ref(), nullptr, c->partial, c->st));
   CK(colsum(c, B, DL_S_RR0));
+  if (x_init) {
+    CK(normal_op(c, B, hi, f, x->ref(), F.th1->ref(), F.tq->ref(), F.th2->ref(), F.ax->ref(), nullptr));
+    CK(dl::xmy_norm(B, hi, F.rh->ref(), b->ref(), F.ax->ref(), nullptr, c->partial, c->st));
+    CK(colsum(c, B, DL_S_TMP));
+  } else {
+    CK(dl::zero(B, hi, x->ref(), nullptr, c->st));
+  }
   CGState h;
   if ((s = download_state(c, n, h)) != DL_OK) return s;
+  const double tol2_ = prm.tol * prm.tol;
   for (int i = 0; i < n; ++i) {
-    double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
-    h.S[DL_S_RR * DL_NCMAX + i] = rr0;
-    h.S[DL_S_MAXR * DL_NCMAX + i] = sqrt(rr0);
-    h.active[i] = rr0 > 0.0 ? 1 : 0;
+    const double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+    const double rr = x_init ? h.S[DL_S_TMP * DL_NCMAX + i] : rr0;
+    h.S[DL_S_RR * DL_NCMAX + i] = rr;
+    h.S[DL_S_MAXR * DL_NCMAX + i] = sqrt(rr);
+    h.active[i] = (rr0 > 0.0 && rr > tol2_ * rr0) ? 1 : 0;
     h.flags[i] = 0;
   }
   h.iters.assign(n, 0);
   CK(cudaMemcpyAsync(c->iters, h.iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
   if ((s = upload_state(c, n, h)) != DL_OK) return s;
-  CK(dl::copy(B, lo, hi, F.r->ref(), b->ref(), nullptr, c->st));
+  CK(dl::copy(B, lo, hi, F.r->ref(), x_init ? F.rh->ref() : b->ref(), nullptr, c->st));
   CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), nullptr, c->st));
   CK(dl::zero(B, lo, F.y->ref(), nullptr, c->st));
   const double tol2 = prm.tol * prm.tol;
@@ -475,7 +483,7 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
   const long long body_kernels = ge ? ge->kernels : 0;
   std::vector<int> finalized(n, 0), notconv(n, 0);
   for (int i = 0; i < n; ++i)
-    if (!h.active[i]) finalized[i] = 1;  // zero right-hand side: x = 0
+    if (!h.active[i]) finalized[i] = 1;  // zero right-hand side (x = 0) or an initial guess within tolerance
   int n_rel = 0;
   auto t0 = std::chrono::steady_clock::now();
   bool breakdown = false;
@@ -646,7 +654,7 @@ int dtype_prec(int dtype) { return dtype == DL_C128 ? P64 : P32; }
 // From a full-lattice source (b_e, b_o, precision hi) to the solution
 // (x_e, psi_o, precision hi).
 dl_status solve_internal(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b_e, Field* b_o, Field* x_e,
-                         Field* psi_o, bool final_check, dl_solve_stats* stats) {
+                         Field* psi_o, bool final_check, dl_solve_stats* stats, bool x_init = false) {
   const int hi = prm.prec_hi, f = prm.flavour;
   dl_status s;
   Field *tmp_o, *bhat, *bn, *t2;
@@ -663,7 +671,7 @@ dl_status solve_internal(dl_ctx* c, const Batch& B, const dl_solve_params& prm, 
   // bn = Mhat^dag bhat
   CK(stage1(c, B, hi, true, f, bhat->ref(), t2->ref(), nullptr));
   CK(stage2(c, B, hi, true, f, t2->ref(), bhat->ref(), bn->ref(), nullptr, nullptr));
-  dl_status rs = run_cg(c, B, prm, bn, x_e, final_check, stats, nullptr);
+  dl_status rs = run_cg(c, B, prm, bn, x_e, final_check, stats, nullptr, x_init);
   if (rs < 0) return rs;
   // psi_o = R_oo^{-1} (b_o + kappa D_oe x_e)
   EpiSet Er = epiB(B, CK_K, 2, f, 0, 0);
@@ -1281,9 +1289,16 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
       return s2;
     CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, first, 0, c->st));
     CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, first, 0, c->st));
+    bool guess = false;
+    if (hp && prm->hp_guess) {  // start from the LP solution of the same noise (same block, FP32 field)
+      Field* lp_xe;
+      if ((s2 = ensure_field(c, "ts_xe32", P32, B, &lp_xe)) != DL_OK) return s2;
+      CK(dl::copy(B, P64, P32, xe->ref(), lp_xe->ref(), nullptr, c->st));
+      guess = true;
+    }
     auto t0 = std::chrono::steady_clock::now();
     dl_status rs = (!hp && prm->lp_net) ? nn_map_block(prm->lp_net, c, B, ee, eo, xe, po)
-                                        : solve_internal(c, B, sp, ee, eo, xe, po, false, st);
+                                        : solve_internal(c, B, sp, ee, eo, xe, po, false, st, guess);
     if (rs < 0) return rs;
     if (rs == DL_NOT_CONVERGED) any_nc = true;
     CK(cudaStreamSynchronize(c->st));

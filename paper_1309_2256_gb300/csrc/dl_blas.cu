@@ -131,7 +131,7 @@ __global__ void sum_partials_kernel(Batch B, const double* __restrict__ partial,
       l = k;
       col = gc - B.lat[k].rhs_base;
     }
-  __shared__ double s[256];
+  __shared__ double s[1024];
   double acc = 0.0;
   if (l >= 0)
     for (int b = B.blk_begin[l] + threadIdx.x; b < B.blk_begin[l + 1]; b += blockDim.x)
@@ -425,7 +425,7 @@ cudaError_t sum_partials(const Batch& Bin, const double* partial, double* out, i
   grid_of(B);
   if (ncols_total <= 0) return cudaSuccess;
   DL_COUNT();
-  sum_partials_kernel<<<ncols_total, 256, 0, st>>>(B, partial, out, stride, slot);
+  sum_partials_kernel<<<ncols_total, 1024, 0, st>>>(B, partial, out, stride, slot);
   return cudaGetLastError();
 }
 

@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(256, DL_MINB) dslash_staged(Batch B, int out_p
     for (int m = 0; m < 24; ++m) acc[m] = 0;
 #define HOP(D, MU, BWD)                                                                                  \
     {                                                                                                    \
-      R v[24];                                                                                           \
-      SIO<P>::load(inb, inn, nitems, ((long long)snb[(D) * S + sl] << lg) + col, v);                     \
-      hop_term<R, BWD, MU>(acc, v, su + ((D) * S + sl) * 18, BWD ? sb : sf);                             \
+      R v[24], w;                                                                                        \
+      load_hop<P>(inb, inn, nitems, ((long long)snb[(D) * S + sl] << lg) + col, v, w);                   \
+      hop_term<R, BWD, MU>(acc, v, su + ((D) * S + sl) * 18, BWD ? sb : sf, w);                          \
     }
     HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
     HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
@@ -177,13 +177,11 @@ __global__ void __launch_bounds__(256) dslash_kernel(Batch B, int out_parity, fl
     {                                                                                    \
       bool crosses;                                                                      \
       const int nb = neighbour(L, x, y, z, t, D, crosses);                               \
-      R v[24], u[18];                                                                    \
-      SIO<P>::load(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v);             \
+      R v[24], u[18], w;                                                                 \
+      load_hop<P>(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v, w);           \
       GIO<G>::load(gb, L.Vh, BWD ? q : p, MU, BWD ? nb : i, u);                           \
-      if (crosses) {                                                                     \
-        _Pragma("unroll") for (int m = 0; m < 24; ++m) v[m] *= (R)L.tbc;                 \
-      }                                                                                  \
-      hop_term<R, BWD, MU>(acc, v, u, BWD ? sb : sf);                                    \
+      if (crosses) w *= (R)L.tbc;                                                        \
+      hop_term<R, BWD, MU>(acc, v, u, BWD ? sb : sf, w);                                 \
     }
     HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
     HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)

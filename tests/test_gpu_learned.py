@@ -246,12 +246,23 @@ def test_tsm_with_learned_lp_map(dl):
         dl.dl_destroy(ctx)
     minv = np.linalg.inv(op.dense_matrix(links, kappa, amu, 1))
     ws = _to_oracle(w, 3, 8)
+
+    def functional(est, e, s):
+        """The loop functional the TSM applies to any map's output: for the generalised
+        estimator D_W s is taken as eta - 2i kappa amu g5 s (equal for the exact s,
+        and what the GPU evaluates for every map)."""
+        if est == "one_end":
+            xi, phi = loops.g5(s), s
+        else:
+            xi, phi = loops.g5(s), loops.g5(e - 2j * kappa * amu * loops.g5(s))
+        return loops.prefactor(est, kappa, amu) * loops.bilinear(xi, phi).sum(axis=(1, 2, 3))
+
     for k, est in enumerate(("one_end", "gen_one_end")):
         fh, fl = [], []
         for r in range(n_hp + n_lp):
             e = noise.z4_noise(dims, 2000, r)
             s_lp, _ = network.forward(links, ws, e)
-            f = lambda s: loops.prefactor(est, kappa, amu) * loops.bilinear(*loops.pair(est, links, e, s, kappa, amu)).sum(axis=(1, 2, 3))
+            f = lambda s: functional(est, e, s)
             fl.append(f(s_lp))
             if r < n_hp:
                 fh.append(f((minv @ e.ravel()).reshape(e.shape)))
