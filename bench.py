@@ -3,7 +3,7 @@
 
 Workload (32^3 x 64, eps 0.4, kappa 0.1612, a*mu 0.0055, antiperiodic in t):
 the Truncated Solver Method with N_HP = 24 high-precision (CG residual 1e-10,
-FP32 Krylov vectors, FP64 reliable updates at delta = 0.01) and N_LP = 500 low-precision
+FP32 Krylov vectors, FP64 reliable updates at delta = 0.001) and N_LP = 500 low-precision
 (residual 1e-2, 16-bit fixed-point Krylov vectors) solves of the even-odd twisted-mass
 operator, batched 16 right-hand sides per launch, each solution contracted
 into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
@@ -37,7 +37,7 @@ DIMS = (32, 32, 32, 64)
 EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
 N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 16
 TOL_HP, TOL_LP = 1e-10, 1e-2
-DELTA_HP = 0.01  # reliable updates every two decades: FP64 operator applications are ALU-bound on GB300
+DELTA_HP = 0.001  # reliable updates every three decades: each costs a high-precision operator application
 P2MAX = 9
 LINK_SEED, NOISE_SEED = 1002, 2002
 WORKLOAD = "tsm_32x32x32x64"
@@ -306,8 +306,15 @@ def roofline(prof, infos):
     if best is None:
         return None
     peak = peaks["hbm_gbs"]
+    # DRAM bytes (read + write) of the 16-bit stage-3 kernel from one ncu capture of the
+    # 24^3 x 24, 16-column case (profiles/dslash_staged_16bit_cg_24x24x24x24_16rhs.md),
+    # scaled to this launch by its site-columns (traffic is linear in them)
+    traffic = None
+    if best["stage"] == 3 and best["prec"] == "16-bit":
+        per_item = 1002.4e6 / (24 ** 4 // 2 * 16)
+        traffic = int(per_item * Vh * best["cols"])
     return {"bound": "hbm", "achieved": round(best["gbs"], 1), "peak": peak, "unit": "GB/s",
-            "frac": round(best["gbs"] / peak, 4), "traffic": None,
+            "frac": round(best["gbs"] / peak, 4), "traffic": traffic,
             "kernel": f"dslash stage {best['stage']} ({best['prec']} Krylov, {best['cols']:.1f} columns)",
             "bytes_per_launch": int(best["bytes"]), "avg_launch_ms": round(best["avg_ms"], 4),
             "peak_kind": kind + " (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else kind}
@@ -463,7 +470,8 @@ def learned_case(args):
     for b in range(0, args.fresh, 32):
         n = min(32, args.fresh - b)
         dl.dl_noise_z4(ctx, 5000 + cfg["id"], b, n, fresh[b:b + n])
-    fg = dl.dl_fgcr_params(tol=1e-10, max_iter=5000, restart=16, inner_tol=1e-4, flavour=1)
+    fg = dl.dl_fgcr_params(tol=1e-10, max_iter=args.fgcr_max_iter, restart=args.fgcr_restart, inner_tol=1e-4,
+                           flavour=1)
     n_fg = min(args.fresh, args.fgcr_rhs)
     for name, net in (("fgcr_net", nn), ("fgcr_plain", None)):
         x = torch.empty((n_fg, V * 12), dtype=torch.complex128, device="cuda")
@@ -555,6 +563,8 @@ def main():
     ap.add_argument("--fresh", type=int, default=200, help="learned case: fresh noise vectors")
     ap.add_argument("--fgcr-rhs", type=int, default=200, help="learned case: fresh vectors solved by FGCR")
     ap.add_argument("--train-steps", type=int, default=1000, help="learned case: Adam steps")
+    ap.add_argument("--fgcr-restart", type=int, default=64, help="learned case: FGCR directions per cycle")
+    ap.add_argument("--fgcr-max-iter", type=int, default=600, help="learned case: FGCR iterations per solve")
     ap.add_argument("--batch", type=int, default=4, help="learned case: pairs per Adam step")
     ap.add_argument("--lr", type=float, default=1e-3, help="learned case: Adam learning rate")
     args = ap.parse_args()

@@ -355,7 +355,7 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* params, int n_pairs, 
 typedef struct {
   double tol;        /* true relative residual bound */
   int max_iter;      /* inner iterations per right-hand side */
-  int restart;       /* directions per inner cycle, 1..32 */
+  int restart;       /* directions per inner cycle, 1..256 (two FP32 full-lattice fields each) */
   double inner_tol;  /* relative residual reduction per inner cycle */
   int flavour;       /* +1 (u) or -1 (d) */
 } dl_fgcr_params;

@@ -126,11 +126,15 @@ EpiSet epiB(const Batch& B, int ck, int t1, int f1, int t2, int f2) {
     e.b2 = 0.0;
     if (t1) twist_ab_l(L, f1, t1 == 2, e.a1, e.b1);
     if (t2) twist_ab_l(L, f2, t2 == 2, e.a2, e.b2);
-    e.cf = (float)e.c;
-    e.a1f = (float)e.a1;
-    e.b1f = (float)e.b1;
-    e.a2f = (float)e.a2;
-    e.b2f = (float)e.b2;
+    auto split = [](double v, float& f, float& l) {
+      f = (float)v;
+      l = (float)(v - (double)f);
+    };
+    split(e.c, e.cf, e.cl);
+    split(e.a1, e.a1f, e.a1l);
+    split(e.b1, e.b1f, e.b1l);
+    split(e.a2, e.a2f, e.a2l);
+    split(e.b2, e.b2f, e.b2l);
   }
   return E;
 }
@@ -147,7 +151,9 @@ size_t items_of(const Batch& B) {
   return n;
 }
 
-int grec_of(const dl_ctx* c, int prec) { return prec == P64 ? 18 : (prec == P32 ? c->rec32 : c->rec16); }
+int grec_of(const dl_ctx* c, int prec) {
+  return (prec == P64 || prec == PDF) ? 18 : (prec == P32 ? c->rec32 : c->rec16);
+}
 
 void invalidate_graphs(dl_ctx* c) {
   for (auto& g : c->graphs)
@@ -235,7 +241,7 @@ const FieldRef NOF = {nullptr, nullptr};
 cudaError_t stage1(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRef in_e, FieldRef out_o, const int* mask) {
   int ff = dag ? -f : f;
   EpiSet E = epiB(B, CK_ONE, 2, ff, 0, 0);
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   return dl::dslash(B, prec, grec_of(c, prec), EPI_PLAIN, dag, 1, in_e, NOF, out_o, g, E, mask, nullptr, NOF, NOF, NOF,
                     nullptr, c->st);
 }
@@ -244,7 +250,7 @@ cudaError_t stage2(dl_ctx* c, const Batch& B, int prec, bool dag, int f, FieldRe
                    const int* mask, double* partial) {
   int ff = dag ? -f : f;
   EpiSet E = epiB(B, CK_MK2, 0, 0, 1, ff);
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   return dl::dslash(B, prec, grec_of(c, prec), partial ? EPI_AUX_NORM : EPI_AUX, dag, 0, in_o, aux_e, out_e, g, E, mask,
                     partial, NOF, NOF, NOF, nullptr, c->st);
 }
@@ -305,7 +311,7 @@ cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGField
   DL_CUDA_TRY(stage1(c, B, lo, true, f, F.q->ref(), F.t2->ref(), c->active));
   {
     EpiSet E = epiB(B, CK_MK2, 0, 0, 1, -f);
-    GaugeSet g{c->g64, c->g32, c->g16};
+    GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
     DL_CUDA_TRY(dl::dslash(B, lo, grec_of(c, lo), EPI_CG, true, 0, F.t2->ref(), F.q->ref(), NOF, g, E, c->active,
                            c->partial, F.r->ref(), F.y->ref(), F.p->ref(), c->S + DL_S_ALPHA * DL_NCMAX, c->st));
   }
@@ -319,7 +325,7 @@ cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGField
 // Runs after a solve has finished: it leaves r and y modified, which the next
 // solve re-initialises.
 dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F) {
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   cudaEvent_t* ev = c->pev;
   CK(cudaEventRecord(ev[0], c->st));
   CK(stage1(c, B, lo, false, f, F.p->ref(), F.t1->ref(), nullptr));
@@ -339,11 +345,12 @@ dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGField
   for (int k = 0; k < 4; ++k) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
-    c->prof_ms[k][lo] += ms;
-    c->prof_n[k][lo] += 1;
+    const int slot = lo == PDF ? P64 : lo;
+    c->prof_ms[k][slot] += ms;
+    c->prof_n[k][slot] += 1;
     long long it = 0;
     for (int l = 0; l < B.nlat; ++l) it += (long long)B.lat[l].Vh * B.lat[l].ncol;
-    c->prof_items[k][lo] += it;  // site-column items with every column active
+    c->prof_items[k][slot] += it;  // site-column items with every column active
   }
   return DL_OK;
 }
@@ -487,6 +494,9 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
   int n_rel = 0;
   auto t0 = std::chrono::steady_clock::now();
   bool breakdown = false;
+  // a breakdown in low-precision arithmetic restarts the column from its true residual
+  // (p = r after a reliable update), at most 8 times, when reliable updates are enabled
+  std::vector<int> restarts(n, 0);
   while (true) {
     bool any = false;
     for (int i = 0; i < n; ++i) any |= (h.active[i] != 0);
@@ -522,13 +532,10 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     for (int i = 0; i < n; ++i) {
       if (finalized[i]) continue;
       if (h.flags[i] & DL_FLAG_BREAKDOWN) {
-        if (!breakdown) {
-          char msg[256];
-          snprintf(msg, sizeof(msg), "CG breakdown in column %d after %d iterations (pAp %.3e, rr %.3e, rr_new %.3e)", i,
-                   h.iters[i], h.S[DL_S_PAP * DL_NCMAX + i], h.S[DL_S_RR * DL_NCMAX + i], h.S[DL_S_RRNEW * DL_NCMAX + i]);
-          c->err = msg;
-        }
-        breakdown = true;
+        char msg[256];
+        snprintf(msg, sizeof(msg), "CG breakdown in column %d after %d iterations (pAp %.3e, rr %.3e, rr_new %.3e)", i,
+                 h.iters[i], h.S[DL_S_PAP * DL_NCMAX + i], h.S[DL_S_RR * DL_NCMAX + i], h.S[DL_S_RRNEW * DL_NCMAX + i]);
+        c->err = msg;
         mask[i] = 1;
         need = true;
         continue;
@@ -557,6 +564,28 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     std::vector<double> rr;
     if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) return s;
     CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
+    {
+      std::vector<int> rmask(n, 0);
+      bool any_restart = false;
+      for (int i = 0; i < n; ++i) {
+        if (!mask[i] || !(h.flags[i] & DL_FLAG_BREAKDOWN)) continue;
+        const double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
+        if (prm.delta > 0.0 && restarts[i] < 8 && rr[i] > prm.tol * prm.tol * rr0 && h.iters[i] < prm.max_iter &&
+            std::isfinite(rr[i])) {
+          ++restarts[i];
+          h.flags[i] &= ~DL_FLAG_BREAKDOWN;
+          h.active[i] = 1;
+          rmask[i] = 1;
+          any_restart = true;
+        } else {
+          breakdown = true;
+        }
+      }
+      if (any_restart) {  // p = r (the true residual just copied to the Krylov precision)
+        CK(cudaMemcpyAsync(c->upd, rmask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+        CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), c->upd, c->st));
+      }
+    }
     for (int i = 0; i < n; ++i) {
       if (!mask[i]) continue;
       ++n_rel;
@@ -613,8 +642,9 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
   }
   CK(cudaStreamSynchronize(c->st));
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (c->profiling && c->prof_pending[lo]) {
-    c->prof_pending[lo] = 0;
+  const int plo = lo == PDF ? P64 : lo;  // profile slots: 0 high precision, 1 FP32, 2 16-bit
+  if (c->profiling && plo <= P16 && c->prof_pending[plo]) {
+    c->prof_pending[plo] = 0;
     if ((s = sample_stencil(c, B, lo, f, F)) != DL_OK) return s;
   }
   int maxit = 0;
@@ -664,7 +694,7 @@ dl_status solve_internal(dl_ctx* c, const Batch& B, const dl_solve_params& prm, 
   // bhat_e = b_e + kappa D_eo R_oo^{-1} b_o
   EpiSet Ei = epiB(B, CK_ONE, 2, f, 0, 0);
   CK(dl::twist(B, hi, tmp_o->ref(), b_o->ref(), Ei, nullptr, c->st));
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   EpiSet Ep = epiB(B, CK_K, 0, 0, 0, 0);
   CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, tmp_o->ref(), b_e->ref(), bhat->ref(), g, Ep, nullptr, nullptr,
                 NOF, NOF, NOF, nullptr, c->st));
@@ -731,10 +761,11 @@ dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int w
   double2* G3 = G2 + nG2;
   double2* ph = G3 + nG3;
   if (L.X > (int)nph || L.Y > (int)nph || L.Z > (int)nph) return fail(c, DL_ERR_ARG, "spatial extent too large");
-  const int fp32 = fused && prec != P64;  // the unfused fallback keeps every stage in FP64
+  // arithmetic of the DFT buffers: 1 float, 2 double-float, 0 double (the unfused fallback)
+  const int fp32 = !fused ? 0 : (prec == P32 ? 1 : (prec == PDF ? 2 : 0));
   if (fused) {
     CK(dl::contract_x(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
-                      eta_o ? eta_o->ref() : NOF, c->g64, c->g32, c->rec32, mx, G1, c->st));
+                      eta_o ? eta_o->ref() : NOF, prec == PDF ? c->gdf : c->g64, c->g32, c->rec32, mx, G1, c->st));
   } else {
     CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
                           eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
@@ -753,7 +784,7 @@ dl_status bh_power(dl_ctx* c, const Batch& B, int prec, int f, int k, Field* se,
   if ((s = ensure_field(c, "bh_ae", prec, B, &ae)) || (s = ensure_field(c, "bh_ao", prec, B, &ao)) ||
       (s = ensure_field(c, "bh_be", prec, B, &be)) || (s = ensure_field(c, "bh_bo", prec, B, &bo)))
     return s;
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   EpiSet E = epiB(B, CK_MK, 2, f, 0, 0);
   Field *ie = se, *io = so;
   for (int it = 0; it < k; ++it) {
@@ -854,7 +885,7 @@ void dl_destroy(dl_ctx* c) {
   }
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
-  void* ptrs[] = {c->waitc, c->loopctr, c->g64, c->g32, c->g16, c->partial, c->S, c->active, c->flags, c->iters, c->upd, c->misc, c->mom,
+  void* ptrs[] = {c->waitc, c->loopctr, c->g64, c->gdf, c->g32, c->g16, c->partial, c->S, c->active, c->flags, c->iters, c->upd, c->misc, c->mom,
                   c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -889,6 +920,7 @@ dl_status dl_load_gauge_lat(dl_ctx* c, int lat, const double* links, int on_devi
   const size_t nl_total = 2ull * c->Vh_total * 4;
   if (!c->g64) {
     CK(cudaMalloc(&c->g64, nl_total * 9 * sizeof(double2)));  // 144 B per link
+    CK(cudaMalloc(&c->gdf, nl_total * 9 * sizeof(float4)));   // 144 B per link
     CK(cudaMalloc(&c->g32, nl_total * 3 * sizeof(float4)));    // up to 48 B per link
     CK(cudaMalloc(&c->g16, nl_total * 3 * sizeof(uint2)));     // up to 24 B per link
   }
@@ -914,9 +946,10 @@ dl_status dl_load_gauge_lat(dl_ctx* c, int lat, const double* links, int on_devi
   // byte offsets of this lattice in each gauge array (chunk bytes x chunks per link x 8 links per parity site)
   const size_t o = (size_t)LI.gsite_off;
   char* g64 = (char*)c->g64 + o * 16 * 9 * 8;
+  char* gdf = (char*)c->gdf + o * 16 * 9 * 8;
   char* g32 = (char*)c->g32 + o * 16 * (recon_f32 == 12 ? 3 : 2) * 8;
   char* g16 = (char*)c->g16 + o * (recon_f16 == 12 ? 8 * 3 : 16 * 1) * 8;
-  cudaError_t e = dl::pack_gauge(L, dlinks, g64, g32, recon_f32, g16, recon_f16, c->st);
+  cudaError_t e = dl::pack_gauge(L, dlinks, g64, gdf, g32, recon_f32, g16, recon_f16, c->st);
   if (tmp) {
     cudaStreamSynchronize(c->st);
     cudaFree(tmp);
@@ -978,6 +1011,7 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
       (dtype != DL_C128 && dtype != DL_C64))
     return fail(c, DL_ERR_ARG, "dl_apply: bad argument");
   if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");
+  prec = internal_prec(prec);
   if ((s = enter(c)) != DL_OK) return s;
   Batch B = make_batch(c, n);
   if ((s = ensure_partial(c, B)) != DL_OK) return s;
@@ -993,7 +1027,7 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
     CK(dl::pack(B, prec, 0, ae->ref(), aux, dtype, c->st));
     CK(dl::pack(B, prec, 1, ao->ref(), aux, dtype, c->st));
   }
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   const int gr = grec_of(c, prec);
   auto D = [&](int epi_kind, bool dag, int par, Field* src, Field* ax, Field* dst, const EpiSet& E) {
     return dl::dslash(B, prec, gr, epi_kind, dag, par, src->ref(), ax ? ax->ref() : NOF, dst->ref(), g, E, nullptr,
@@ -1061,6 +1095,10 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
       prm->delta < 0.0 || prm->delta >= 1.0)
     return fail(c, DL_ERR_ARG, "dl_solve: bad parameters");
   if ((s = enter(c)) != DL_OK) return s;
+  dl_solve_params sp = *prm;
+  sp.prec_hi = internal_prec(prm->prec_hi);
+  sp.prec_lo = internal_prec(prm->prec_lo);
+  prm = &sp;
   const int hi = prm->prec_hi;
   Batch B = make_batch(c, n);
   if ((s = ensure_partial(c, B)) != DL_OK) return s;
@@ -1085,7 +1123,7 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
       return s;
     CK(dl::pack(B, hi, 0, bh_e->ref(), src, dtype, c->st));
     CK(dl::pack(B, hi, 1, bh_o->ref(), src, dtype, c->st));
-    GaugeSet g{c->g64, c->g32, c->g16};
+    GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
     EpiSet E = epiB(B, CK_MK, 0, 0, 1, prm->flavour);
     CK(dl::dslash(B, hi, grec_of(c, hi), EPI_AUX, false, 0, po->ref(), xe->ref(), re->ref(), g, E, nullptr, nullptr, NOF,
                   NOF, NOF, nullptr, c->st));
@@ -1169,7 +1207,7 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
     return fail(c, DL_ERR_ARG, "estimator needs eta");
   if (est == DL_EST_HPE && with_deriv) return fail(c, DL_ERR_ARG, "the HPE estimator is local only");
   if ((s = enter(c)) != DL_OK) return s;
-  const int prec = dtype_prec(dtype);
+  const int prec = dtype == DL_C128 ? PDF : P32;  // complex128 inputs are contracted in double-float
   Batch B = make_batch(c, n);
   Field *se, *so, *ee, *eo;
   if ((s = ensure_field(c, "ct_se", prec, B, &se)) || (s = ensure_field(c, "ct_so", prec, B, &so)) ||
@@ -1268,12 +1306,12 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
 
   // one precision's pipeline: noise -> solve -> contractions into `out`
   auto run_block = [&](int n, uint64_t first, bool hp, double2* out, double* obs, dl_solve_stats* st) -> dl_status {
-    const int hi = hp ? P64 : P32;
+    const int hi = hp ? PDF : P32;
     dl_solve_params sp;
     sp.tol = hp ? prm->tol_hp : prm->tol_lp;
     sp.max_iter = prm->max_iter;
     sp.prec_hi = hi;
-    sp.prec_lo = hp ? prm->prec_hp_lo : prm->prec_lp_lo;
+    sp.prec_lo = internal_prec(hp ? prm->prec_hp_lo : prm->prec_lp_lo);
     sp.delta = hp ? prm->delta_hp : 0.0;
     sp.flavour = 1;
     sp.chunk = prm->chunk > 0 ? prm->chunk : 16;
@@ -1293,7 +1331,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     if (hp && prm->hp_guess) {  // start from the LP solution of the same noise (same block, FP32 field)
       Field* lp_xe;
       if ((s2 = ensure_field(c, "ts_xe32", P32, B, &lp_xe)) != DL_OK) return s2;
-      CK(dl::copy(B, P64, P32, xe->ref(), lp_xe->ref(), nullptr, c->st));
+      CK(dl::copy(B, hi, P32, xe->ref(), lp_xe->ref(), nullptr, c->st));
       guess = true;
     }
     auto t0 = std::chrono::steady_clock::now();
@@ -1398,7 +1436,7 @@ dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, v
     return fail(c, DL_ERR_ARG, "dl_batch_loops: bad parameters");
   dl_status s;
   if ((s = enter(c)) != DL_OK) return s;
-  const int hi = prm->prec_hi;
+  const int hi = internal_prec(prm->prec_hi);
   dl_batch_info inf;
   memset(&inf, 0, sizeof(inf));
   auto t0 = std::chrono::steady_clock::now();
@@ -1416,7 +1454,7 @@ dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, v
     sp.tol = tol;
     sp.max_iter = max_iter;
     sp.prec_hi = hi;
-    sp.prec_lo = prm->prec_lo;
+    sp.prec_lo = internal_prec(prm->prec_lo);
     sp.delta = delta;
     sp.flavour = 1;
     sp.chunk = 0;
@@ -1565,6 +1603,7 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
       (dtype != DL_C128 && dtype != DL_C64) || op < DL_OP_M || op > DL_OP_BH)
     return fail(c, DL_ERR_ARG, "dl_apply_noalloc: bad argument");
   if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");
+  prec = internal_prec(prec);
   // seven parity fields (in, out, aux for both parities, one temporary), each
   // 256-byte aligned, must fit the fixed array
   const size_t items = (size_t)c->Vh << ilog2ceil(n);
@@ -1593,7 +1632,7 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
     CK(dl::pack(B, prec, 0, ae, aux, dtype, c->st));
     CK(dl::pack(B, prec, 1, ao, aux, dtype, c->st));
   }
-  GaugeSet g{c->g64, c->g32, c->g16};
+  GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   const int gr = grec_of(c, prec);
   auto D = [&](int epi_kind, bool dag, int par, FieldRef src, FieldRef ax, FieldRef dst, const EpiSet& E) {
     return dl::dslash(B, prec, gr, epi_kind, dag, par, src, ax, dst, g, E, nullptr, nullptr, NOF, NOF, NOF, nullptr,

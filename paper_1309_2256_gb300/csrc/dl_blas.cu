@@ -107,7 +107,7 @@ __global__ void twist_kernel(Batch B, FieldRef out, FieldRef in, EpiSet ep, cons
   typedef typename SIO<P>::real R;
   R v[24];
   SIO<P>::load(seg_ptr<P>(in, L), seg_norm(in, L), nitems, j, v);
-  twist_apply<R>(v, epc<R>(ep.e[l].a1, ep.e[l].a1f), epc<R>(ep.e[l].b1, ep.e[l].b1f));
+  twist_apply<R>(v, epc<R>(ep.e[l].a1, ep.e[l].a1f, ep.e[l].a1l), epc<R>(ep.e[l].b1, ep.e[l].b1f, ep.e[l].b1l));
   SIO<P>::store(seg_ptr_w<P>(out, L), seg_norm(out, L), nitems, j, v);
 }
 
@@ -349,6 +349,7 @@ static int grid_of(Batch& B) { return blocks_for(B, 256); }
     case P32: { constexpr int PP = P32; CALL; } break; \
     case P16: { constexpr int PP = P16; CALL; } break; \
     case PBF: { constexpr int PP = PBF; CALL; } break; \
+    case PDF: { constexpr int PP = PDF; CALL; } break; \
     default: return cudaErrorInvalidValue; \
   }
 
@@ -359,6 +360,7 @@ cudaError_t copy(const Batch& Bin, int pd, int ps, FieldRef dst, FieldRef src, c
 #define CP(a, b) if (pd == a && ps == b) { DL_COUNT(); copy_kernel<a, b><<<g, 256, 0, st>>>(B, dst, src, mask); return cudaGetLastError(); }
   CP(P64, P64) CP(P64, P32) CP(P64, P16) CP(P32, P64) CP(P32, P32) CP(P32, P16) CP(P16, P64) CP(P16, P32) CP(P16, P16)
   CP(PBF, P64) CP(P64, PBF) CP(PBF, P32) CP(P32, PBF)
+  CP(PDF, PDF) CP(PDF, P64) CP(P64, PDF) CP(PDF, P32) CP(P32, PDF) CP(PDF, P16) CP(P16, PDF)
 #undef CP
   return cudaErrorInvalidValue;
 }
@@ -368,7 +370,7 @@ cudaError_t accum(const Batch& Bin, int ph, int pl, FieldRef x, FieldRef y, cons
   int g = grid_of(B);
   if (!g) return cudaSuccess;
 #define AC(a, b) if (ph == a && pl == b) { DL_COUNT(); accum_kernel<a, b><<<g, 256, 0, st>>>(B, x, y, mask, zero_y); return cudaGetLastError(); }
-  AC(P64, P64) AC(P64, P32) AC(P64, P16) AC(P32, P32) AC(P32, P16)
+  AC(P64, P64) AC(P64, P32) AC(P64, P16) AC(P32, P32) AC(P32, P16) AC(PDF, PDF) AC(PDF, P32) AC(PDF, P16)
 #undef AC
   return cudaErrorInvalidValue;
 }

@@ -603,6 +603,7 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
     return cudaGetLastError();                                                                              \
   }
   CS(P64, 0) CS(P64, 1) CS(P64, 2) CS(P64, 3) CS(P32, 0) CS(P32, 1) CS(P32, 2) CS(P32, 3)
+  CS(PDF, 0) CS(PDF, 1) CS(PDF, 2) CS(PDF, 3)
 #undef CS
   return cudaErrorInvalidValue;
 }
@@ -631,6 +632,8 @@ cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, Field
   if (prec == PR && mode == MD) {                                                                                  \
     if (PR == P64) {                                                                                               \
       if (with_deriv) CXK(PR, MD, true, double, G64R18, g64) else CXK(PR, MD, false, double, G64R18, g64)         \
+    } else if (PR == PDF) {                                                                                        \
+      if (with_deriv) CXK(PR, MD, true, dfloat, GDF18, g64) else CXK(PR, MD, false, dfloat, GDF18, g64)           \
     } else if (rec32 == 12) {                                                                                      \
       if (with_deriv) CXK(PR, MD, true, float, G32R12, g32) else CXK(PR, MD, false, float, G32R12, g32)           \
     } else {                                                                                                       \
@@ -639,6 +642,7 @@ cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, Field
   }
   CX(P64, 0) CX(P64, 1) CX(P64, 2) CX(P64, 3)
   CX(P32, 0) CX(P32, 1) CX(P32, 2) CX(P32, 3)
+  CX(PDF, 0) CX(PDF, 1) CX(PDF, 2) CX(PDF, 3)
 #undef CX
 #undef CXK
   return cudaErrorInvalidValue;
@@ -653,9 +657,14 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
   if (g <= 0) return cudaSuccess;
   if (g > 0x7fffffffLL) return cudaErrorInvalidValue;
   DL_COUNT();
-  if ((size_t)(len * DL_DFT_TILE + len) * 2 * (fp32 ? sizeof(float) : sizeof(double)) > 200000)
+  if ((size_t)(len * DL_DFT_TILE + len) * 2 * (fp32 == 1 ? sizeof(float) : sizeof(double)) > 200000)
     return cudaErrorInvalidValue;  // extents up to ~190 (FP64) / ~380 (FP32) sites
-  if (fp32) {  // in and out hold float pairs
+  if (fp32 == 2) {  // double-float pairs
+    const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(dfloat);
+    cudaFuncSetAttribute(dft_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    dft_kernel<dfloat><<<(int)g, 256, smem, st>>>((const RPair<dfloat>*)in, (RPair<dfloat>*)out, nb, len, stride, m,
+                                                 phase);
+  } else if (fp32 == 1) {  // in and out hold float pairs
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(float);
     cudaFuncSetAttribute(dft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
     dft_kernel<float><<<(int)g, 256, smem, st>>>((const RPair<float>*)in, (RPair<float>*)out, nb, len, stride, m, phase);
@@ -676,7 +685,11 @@ cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int*
   long long tot = (long long)L.ncol * L.T * np * nd * 16;
   if (tot == 0) return cudaSuccess;
   DL_COUNT();
-  if (fp32)
+  if (fp32 == 2)
+    finalize_kernel<dfloat><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
+                                                                     (const RPair<dfloat>*)G3, pre_re, pre_im, out,
+                                                                     accumulate);
+  else if (fp32 == 1)
     finalize_kernel<float><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
                                                                     (const RPair<float>*)G3, pre_re, pre_im, out,
                                                                     accumulate);

@@ -22,13 +22,13 @@ __device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDes
                                            int col, const FieldRef& aux, const FieldRef& out, const FieldRef& cr,
                                            const FieldRef& cy, const FieldRef& cp, const double* alpha) {
   R red = 0;  // this site-column's |.|^2 in R; the sums over sites are FP64
-  const R c = epc<R>(e.c, e.cf);
+  const R c = epc<R>(e.c, e.cf, e.cl);
 #pragma unroll
   for (int m = 0; m < 24; ++m) acc[m] *= c;
   R v[24];
   if (EPI != EPI_PLAIN) {
     SIO<P>::load(seg_ptr<P>(aux, L), seg_norm(aux, L), nitems, j, v);
-    twist_apply<R>(v, epc<R>(e.a2, e.a2f), epc<R>(e.b2, e.b2f));
+    twist_apply<R>(v, epc<R>(e.a2, e.a2f, e.a2l), epc<R>(e.b2, e.b2f, e.b2l));
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] += v[m];
   }
@@ -47,7 +47,7 @@ __device__ __forceinline__ double epilogue(R acc[24], const Epi& e, const LatDes
     for (int m = 0; m < 24; ++m) v[m] += al * acc[m];
     SIO<P>::store(seg_ptr_w<P>(cy, L), seg_norm(cy, L), nitems, j, v);
   } else {
-    twist_apply<R>(acc, epc<R>(e.a1, e.a1f), epc<R>(e.b1, e.b1f));
+    twist_apply<R>(acc, epc<R>(e.a1, e.a1f, e.a1l), epc<R>(e.b1, e.b1f, e.b1l));
     if (EPI == EPI_AUX_NORM) {
 #pragma unroll
       for (int m = 0; m < 24; ++m) red += acc[m] * acc[m];
@@ -82,8 +82,12 @@ __device__ __forceinline__ int neighbour(const LatDesc& L, int x, int y, int z, 
 #define DL_MINB 4  // resident CTAs per SM the staged stencil is compiled for (best of 2, 3, 4 measured)
 #endif
 
+#ifndef DL_MINB_HI
+#define DL_MINB_HI 2  // the same for the FP64 and double-float kernels (twice the registers per value)
+#endif
+
 template <int P, int G, int EPI>
-__global__ void __launch_bounds__(256, DL_MINB) dslash_staged(Batch B, int out_parity, float sgn_fwd, FieldRef in,
+__global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : DL_MINB) dslash_staged(Batch B, int out_parity, float sgn_fwd, FieldRef in,
                                                           FieldRef aux, FieldRef out, const void* __restrict__ gbase,
                                                           EpiSet ep, const int* __restrict__ active,
                                                           double* __restrict__ partial, FieldRef cr, FieldRef cy,
@@ -258,6 +262,10 @@ cudaError_t dslash(const Batch& Bin, int prec, int grec, int epi, bool dag, int 
   if (prec == P64) {
     if (grec != 18) return cudaErrorInvalidValue;
     return launch_pg<P64, G64R18>(B, grid, epi, sgn, out_parity, in, aux, out, g.g64, ep, active, partial, cr, cy, cp, alpha, st);
+  }
+  if (prec == PDF) {
+    if (grec != 18 || !g.gdf) return cudaErrorInvalidValue;
+    return launch_pg<PDF, GDF18>(B, grid, epi, sgn, out_parity, in, aux, out, g.gdf, ep, active, partial, cr, cy, cp, alpha, st);
   }
   if (prec == P32) {
     if (grec == 12)

@@ -30,7 +30,11 @@ inline int ilog2ceil(int n) {
   return l;
 }
 
-inline size_t chunk_bytes(int prec) { return prec == P64 ? 192 : (prec == P32 ? 96 : 48); }
+inline size_t chunk_bytes(int prec) { return (prec == P64 || prec == PDF) ? 192 : (prec == P32 ? 96 : 48); }
+
+// The API's FP64 precision as the kernels run it: double-float arithmetic on
+// FP32 units (dl_df.cuh), since GB300's FP64 rate is a small fraction of FP32.
+inline int internal_prec(int api_prec) { return api_prec == DL_F64 ? PDF : api_prec; }
 
 struct LatInfo {
   int dims[4];
@@ -52,6 +56,7 @@ struct dl_ctx {
   double kappa = 0.125, amu = 0.0, tbc = -1.0;
   int rec32 = 12, rec16 = 8;
   void* g64 = nullptr;
+  void* gdf = nullptr;  // double-float copy of the FP64 links (same layout, 144 B per link)
   void* g32 = nullptr;
   void* g16 = nullptr;
   bool has_gauge = false;

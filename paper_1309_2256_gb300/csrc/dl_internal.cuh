@@ -21,6 +21,8 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include "dl_df.cuh"
 #include <stdint.h>
 
 #include <string>
@@ -28,7 +30,10 @@
 #define DL_MAX_LAT 16
 #define DL_MAXC 32  // max columns (right-hand sides) per lattice segment
 
-enum { P64 = 0, P32 = 1, P16 = 2, PBF = 3 };  // PBF: bfloat16 activations of the network
+// Storage formats: P64 FP64 (natural-format input/output), P32 FP32, P16 16-bit
+// fixed point, PBF bfloat16 (network activations), PDF double-float (the
+// high-precision arithmetic of the solver on GB300, see dl_df.cuh).
+enum { P64 = 0, P32 = 1, P16 = 2, PBF = 3, PDF = 4 };
 
 // ---------------------------------------------------------------- batch
 struct LatDesc {
@@ -171,6 +176,26 @@ template <> struct SIO<P16> {
   }
 };
 
+// double-float: 12 chunks of (re.hi, re.lo, im.hi, im.lo), 192 bytes like FP64
+template <> struct SIO<PDF> {
+  typedef dfloat real;
+  static constexpr int K = 12;
+  __device__ static __forceinline__ void load(const void* b, const float*, long long st, long long j, dfloat v[24]) {
+    const float4* p = (const float4*)b;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float4 c = __ldg(p + k * st + j);
+      v[2 * k] = dfloat(c.x, c.y);
+      v[2 * k + 1] = dfloat(c.z, c.w);
+    }
+  }
+  __device__ static __forceinline__ void store(void* b, float*, long long st, long long j, const dfloat v[24]) {
+    float4* p = (float4*)b;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k * st + j] = make_float4(v[2 * k].hi, v[2 * k].lo, v[2 * k + 1].hi, v[2 * k + 1].lo);
+  }
+};
+
 // Neighbour spinor of the stencil as values v and a common factor w with
 // spinor = w v: the 16-bit format's per-site scale is applied once to the
 // hop's result (folded into the accumulation) instead of to 24 inputs.
@@ -249,7 +274,7 @@ __device__ __forceinline__ float* seg_norm(const FieldRef& f, const LatDesc& L) 
 }
 
 // ---------------------------------------------------------------- gauge IO
-enum { G64R18 = 0, G32R12 = 1, G32R8 = 2, G16R12 = 3, G16R8 = 4 };
+enum { G64R18 = 0, G32R12 = 1, G32R8 = 2, G16R12 = 3, G16R8 = 4, GDF18 = 5 };
 
 template <int G> struct GIO;
 
@@ -341,6 +366,21 @@ template <> struct GIO<G32R8> {
     recon8(c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, u);
   }
 };
+// double-float links, all 18 reals: 9 chunks of (re.hi, re.lo, im.hi, im.lo)
+template <> struct GIO<GDF18> {
+  typedef dfloat real;
+  static constexpr int GK = 9;
+  typedef float4 chunk;
+  __device__ static __forceinline__ void load(const void* b, int Vh, int p, int mu, int i, dfloat u[18]) {
+    const float4* g = (const float4*)b + (size_t)((p * 4 + mu) * 9) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float4 c = __ldg(g + (size_t)k * Vh);
+      u[2 * k] = dfloat(c.x, c.y);
+      u[2 * k + 1] = dfloat(c.z, c.w);
+    }
+  }
+};
 // 16-bit links: fixed point q / 32767 stored offset by 32768 like the spinors
 // (entries of an SU(3) matrix lie in [-1, 1]; recon-8 angles are stored / pi).
 template <> struct GIO<G16R12> {
@@ -384,6 +424,12 @@ __device__ __forceinline__ const void* gauge_seg(const void* base, const LatDesc
 // (adjoint if DAGU):  acc += w (1 + s gamma_mu) U psi.
 // With G_mu the upper-right block of gamma_mu (G_k = -i sigma_k, G_t = 1):
 //   h = psi_up + s G psi_dn,  chi = U h,  acc_up += chi,  acc_dn += s G^dagger chi.
+// s x for a projector sign s = +-1, and w x for the hop's common factor w: a
+// multiplication in FP32/FP64, a sign flip for double-float (whose storage has
+// no scale, so w = +-1 there).
+template <typename R> __device__ __forceinline__ R sgn_mul(R s, R x) { return s * x; }
+template <> __device__ __forceinline__ dfloat sgn_mul<dfloat>(dfloat s, dfloat x) { return s.hi > 0.f ? x : -x; }
+
 template <typename R, bool DAGU, int mu>
 __device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18], R s, R w) {
   R h[12];  // [spin 0..1][colour][re,im]
@@ -395,17 +441,17 @@ __device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18]
     R d3r = v[18 + 2 * c], d3i = v[18 + 2 * c + 1];  // spin 3
     R h0r, h0i, h1r, h1i;
     if (mu == 0) {        // G = [[0,-i],[-i,0]]: (G d)_0 = -i d3, (G d)_1 = -i d2
-      h0r = u0r + s * d3i; h0i = u0i - s * d3r;
-      h1r = u1r + s * d2i; h1i = u1i - s * d2r;
+      h0r = u0r + sgn_mul(s, d3i); h0i = u0i - sgn_mul(s, d3r);
+      h1r = u1r + sgn_mul(s, d2i); h1i = u1i - sgn_mul(s, d2r);
     } else if (mu == 1) { // G = [[0,-1],[1,0]]: (G d)_0 = -d3, (G d)_1 = d2
-      h0r = u0r - s * d3r; h0i = u0i - s * d3i;
-      h1r = u1r + s * d2r; h1i = u1i + s * d2i;
+      h0r = u0r - sgn_mul(s, d3r); h0i = u0i - sgn_mul(s, d3i);
+      h1r = u1r + sgn_mul(s, d2r); h1i = u1i + sgn_mul(s, d2i);
     } else if (mu == 2) { // G = diag(-i, i): (G d)_0 = -i d2, (G d)_1 = i d3
-      h0r = u0r + s * d2i; h0i = u0i - s * d2r;
-      h1r = u1r - s * d3i; h1i = u1i + s * d3r;
+      h0r = u0r + sgn_mul(s, d2i); h0i = u0i - sgn_mul(s, d2r);
+      h1r = u1r - sgn_mul(s, d3i); h1i = u1i + sgn_mul(s, d3r);
     } else {              // G = 1
-      h0r = u0r + s * d2r; h0i = u0i + s * d2i;
-      h1r = u1r + s * d3r; h1i = u1i + s * d3i;
+      h0r = u0r + sgn_mul(s, d2r); h0i = u0i + sgn_mul(s, d2i);
+      h1r = u1r + sgn_mul(s, d3r); h1i = u1i + sgn_mul(s, d3i);
     }
     h[2 * c] = h0r; h[2 * c + 1] = h0i;
     h[6 + 2 * c] = h1r; h[6 + 2 * c + 1] = h1i;
@@ -429,12 +475,12 @@ __device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18]
       chi[6 * sp + 2 * a + 1] = im;
     }
   }
-  const R sw = s * w;
+  const R sw = sgn_mul(s, w);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     R c0r = chi[2 * c], c0i = chi[2 * c + 1], c1r = chi[6 + 2 * c], c1i = chi[6 + 2 * c + 1];
-    acc[2 * c] += w * c0r; acc[2 * c + 1] += w * c0i;
-    acc[6 + 2 * c] += w * c1r; acc[6 + 2 * c + 1] += w * c1i;
+    acc[2 * c] += sgn_mul(w, c0r); acc[2 * c + 1] += sgn_mul(w, c0i);
+    acc[6 + 2 * c] += sgn_mul(w, c1r); acc[6 + 2 * c + 1] += sgn_mul(w, c1i);
     R l2r, l2i, l3r, l3i;  // G^dagger chi
     if (mu == 0) {        // G^+ = [[0,i],[i,0]]: (G^+ c)_0 = i c1, (G^+ c)_1 = i c0
       l2r = -c1i; l2i = c1r; l3r = -c0i; l3i = c0r;
@@ -445,8 +491,8 @@ __device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18]
     } else {
       l2r = c0r; l2i = c0i; l3r = c1r; l3i = c1i;
     }
-    acc[12 + 2 * c] += sw * l2r; acc[12 + 2 * c + 1] += sw * l2i;
-    acc[18 + 2 * c] += sw * l3r; acc[18 + 2 * c + 1] += sw * l3i;
+    acc[12 + 2 * c] += sgn_mul(sw, l2r); acc[12 + 2 * c + 1] += sgn_mul(sw, l2i);
+    acc[18 + 2 * c] += sgn_mul(sw, l3r); acc[18 + 2 * c + 1] += sgn_mul(sw, l3i);
   }
 }
 
@@ -497,14 +543,16 @@ struct DevBuf {
 //   out = T1 (c * D^{(dag)} in + T2 aux),  T = a + i b gamma_5
 struct Epi {
   double c, a1, b1, a2, b2;
-  float cf, a1f, b1f, a2f, b2f;  // the same coefficients rounded once to FP32 (FP32 and 16-bit kernels)
+  float cf, a1f, b1f, a2f, b2f;       // the same coefficients rounded once to FP32 (FP32 and 16-bit kernels)
+  float cl, a1l, b1l, a2l, b2l;       // and the remainders: (xf, xl) is the double-float value
 };
 // An epilogue coefficient in the kernel's arithmetic type: GB300 issues FP64
 // (and FP64<->FP32 conversion) instructions at a small fraction of the FP32
-// rate, so the FP32 kernels read the pre-rounded copy.
-template <typename R> __device__ __forceinline__ R epc(double d, float f);
-template <> __device__ __forceinline__ double epc<double>(double d, float) { return d; }
-template <> __device__ __forceinline__ float epc<float>(double, float f) { return f; }
+// rate, so the FP32 and double-float kernels read pre-split copies.
+template <typename R> __device__ __forceinline__ R epc(double d, float f, float l);
+template <> __device__ __forceinline__ double epc<double>(double d, float, float) { return d; }
+template <> __device__ __forceinline__ float epc<float>(double, float f, float) { return f; }
+template <> __device__ __forceinline__ dfloat epc<dfloat>(double, float f, float l) { return dfloat(f, l); }
 struct EpiSet {
   Epi e[DL_MAX_LAT];
 };
@@ -515,6 +563,7 @@ struct GaugeSet {
   const void* g64;
   const void* g32;
   const void* g16;
+  const void* gdf;  // double-float copy of the FP64 links
 };
 
 // Every kernel launch is counted (host side) for the launch statistics of the C ABI.

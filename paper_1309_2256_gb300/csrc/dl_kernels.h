@@ -42,15 +42,16 @@ cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void*
 cudaError_t unpack(const Batch& B, int prec, int parity, void* natural, FieldRef src, int dtype, cudaStream_t st);
 cudaError_t noise_z4(const Batch& B, int prec, int parity, FieldRef dst, unsigned long long seed,
                      unsigned long long first, int quadrant, cudaStream_t st);
-cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* g32, int rec32, void* g16, int rec16,
-                       cudaStream_t st);
+cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* gdf, void* g32, int rec32, void* g16,
+                       int rec16, cudaStream_t st);
 
 // contractions
 cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                            FieldRef eta_o, const void* g64, double2* W, cudaStream_t st);
 cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, long long stride, int m, double2* phase,
                      int fp32, cudaStream_t st);
-// G1 (and the DFT passes' buffers) hold float pairs for prec != P64, double pairs for P64
+// G1 (and the DFT passes' buffers) hold float pairs for P32, double-float pairs for PDF
+// and double pairs for P64; dft_pass / contract_finalize take the kind as fp32 = 1 / 2 / 0
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                        FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* G1,
                        cudaStream_t st);

@@ -129,8 +129,8 @@ __global__ void noise_kernel(Batch B, int parity, FieldRef dst, unsigned long lo
 }
 
 // Gauge compression: thread per lexicographic site, all four directions.
-__global__ void pack_gauge_kernel(LatDesc L, const double2* __restrict__ links, double2* g64, void* g32, int rec32,
-                                  void* g16, int rec16) {
+__global__ void pack_gauge_kernel(LatDesc L, const double2* __restrict__ links, double2* g64, float4* gdf, void* g32,
+                                  int rec32, void* g16, int rec16) {
   const int lex = blockIdx.x * blockDim.x + threadIdx.x;
   const int V = 2 * L.Vh;
   if (lex >= V) return;
@@ -150,6 +150,13 @@ __global__ void pack_gauge_kernel(LatDesc L, const double2* __restrict__ links, 
     if (g64) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) g64[(blk * 9 + k) * Vh + i] = e[k];
+    }
+    if (gdf) {  // double-float: hi = the nearest float, lo = the nearest float to the remainder
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float rh = (float)e[k].x, ih = (float)e[k].y;
+        gdf[(blk * 9 + k) * Vh + i] = make_float4(rh, (float)(e[k].x - (double)rh), ih, (float)(e[k].y - (double)ih));
+      }
     }
     if (g32) {
       float4* g = (float4*)g32;
@@ -195,6 +202,7 @@ namespace dl {
     case P32: { constexpr int PP = P32; CALL; } break; \
     case P16: { constexpr int PP = P16; CALL; } break; \
     case PBF: { constexpr int PP = PBF; CALL; } break; \
+    case PDF: { constexpr int PP = PDF; CALL; } break; \
     default: return cudaErrorInvalidValue; \
   }
 
@@ -226,11 +234,12 @@ cudaError_t noise_z4(const Batch& Bin, int prec, int parity, FieldRef dst, unsig
   return cudaGetLastError();
 }
 
-cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* g32, int rec32, void* g16, int rec16,
-                       cudaStream_t st) {
+cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* gdf, void* g32, int rec32, void* g16,
+                       int rec16, cudaStream_t st) {
   int V = 2 * L.Vh;
   DL_COUNT();
-  pack_gauge_kernel<<<(V + 127) / 128, 128, 0, st>>>(L, (const double2*)links_dev, (double2*)g64, g32, rec32, g16, rec16);
+  pack_gauge_kernel<<<(V + 127) / 128, 128, 0, st>>>(L, (const double2*)links_dev, (double2*)g64, (float4*)gdf, g32, rec32,
+                                                     g16, rec16);
   return cudaGetLastError();
 }
 

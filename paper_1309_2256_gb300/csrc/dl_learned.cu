@@ -401,7 +401,7 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!prm || !src || !sol || n < 1 || n > DL_MAX_RHS || !(prm->tol > 0.0) || prm->max_iter < 1 || prm->restart < 1 ||
-      prm->restart > 32 || !(prm->inner_tol > 0.0 && prm->inner_tol < 1.0) || (prm->flavour != 1 && prm->flavour != -1) ||
+      prm->restart > 256 || !(prm->inner_tol > 0.0 && prm->inner_tol < 1.0) || (prm->flavour != 1 && prm->flavour != -1) ||
       (dtype != DL_C128 && dtype != DL_C64))
     return fail(c, DL_ERR_ARG, "dl_fgcr_solve: bad parameters");
   if (nn && (!valid_nn(nn) || nn->c != c)) return fail(c, DL_ERR_ARG, "dl_fgcr_solve: network of another context");

@@ -42,7 +42,7 @@ def test_block_of_12_solves_and_derivative_loops(lat, lo):
     prm = dl.dl_solve_params(tol=1e-10, max_iter=20000, prec_hi=dl.DL_F64,
                              prec_lo=dl.DL_F16 if lo == "f16" else dl.DL_F32, delta=0.01, flavour=1, chunk=0)
     st, stats = dl.dl_solve(ctx, eta, sol, n, dl.DL_C128, prm)
-    assert st == 0
+    assert st == 0, dl.dl_last_error(ctx)
     assert all(stats.resid[i] < 1e-10 for i in range(n))
     assert all(stats.true_resid[i] < 1e-8 for i in range(n))
     npm = len(dl.dl_momenta(4))
