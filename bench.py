@@ -259,19 +259,22 @@ def plain_fp64_reference(dl, ctx, device, infos, n_hp_s):
     eta = torch.empty((1, V * 12), dtype=torch.complex128, device="cuda")
     sol = torch.empty_like(eta)
     dl.dl_noise_z4(ctx, 5, 0, 1, eta, dl.DL_C128)
-    prm = dl.dl_solve_params(tol=1e-30, max_iter=n_it, prec_hi=dl.DL_F64, prec_lo=dl.DL_F64, delta=0.0, flavour=1,
-                             chunk=n_it)
-    dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)  # warm (graph capture)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, st = dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)
-    torch.cuda.synchronize()
-    t_iter = (time.perf_counter() - t0) / n_it
+    per = {}
+    for name, pr in (("ieee_f64", dl.DL_F64_IEEE), ("double_float", dl.DL_F64)):
+        prm = dl.dl_solve_params(tol=1e-30, max_iter=n_it, prec_hi=pr, prec_lo=pr, delta=0.0, flavour=1, chunk=n_it)
+        dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)  # warm (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dl.dl_solve(ctx, eta, sol, 1, dl.DL_C128, prm)
+        torch.cuda.synchronize()
+        per[name] = (time.perf_counter() - t0) / n_it
+    t_iter = min(per.values())  # the faster FP64 form is the baseline
     it_hp = sum(i.iters_hp for i in infos) / max(1, len(infos) * n_hp_s)
     del eta, sol
-    return {"sec_per_iter": t_iter, "hp_iters": it_hp, "sec_per_estimate": t_iter * it_hp,
-            "estimates_per_s": 1.0 / (t_iter * it_hp) if it_hp > 0 else None,
-            "how": f"{n_it} CG iterations timed, scaled by the mean HP iteration count"}
+    return {"sec_per_iter": t_iter, "sec_per_iter_by_arithmetic": per, "hp_iters": it_hp,
+            "sec_per_estimate": t_iter * it_hp, "estimates_per_s": 1.0 / (t_iter * it_hp) if it_hp > 0 else None,
+            "how": f"one right-hand side, {n_it} CG iterations timed in IEEE FP64 and in double-float, the faster "
+                   "scaled by the mean HP iteration count"}
 
 
 def roofline(prof, infos):
@@ -397,7 +400,8 @@ def learned_case(args):
     """The learned preconditioner on 16^3 x 32 (eps 0.4, kappa 0.161, a*mu 0.0055): a
     4-layer, 16-channel network (FP32 weights, bfloat16 activations) trained with Adam
     on (Z4 noise, FP64-accurate solution) pairs from the plain solver, then on fresh
-    noise: flexible GCR to 1e-10 with and without it against the mixed-precision CG,
+    noise: flexible GCR on the normal operator M^+ M (preconditioner N N^+) to 1e-10 with and
+    without it against the mixed-precision CG,
     and the TSM with the network as its LP map against truncated CG."""
     import torch
 
@@ -471,7 +475,7 @@ def learned_case(args):
         n = min(32, args.fresh - b)
         dl.dl_noise_z4(ctx, 5000 + cfg["id"], b, n, fresh[b:b + n])
     fg = dl.dl_fgcr_params(tol=1e-10, max_iter=args.fgcr_max_iter, restart=args.fgcr_restart, inner_tol=1e-4,
-                           flavour=1)
+                           flavour=1, normal=1)
     n_fg = min(args.fresh, args.fgcr_rhs)
     for name, net in (("fgcr_net", nn), ("fgcr_plain", None)):
         x = torch.empty((n_fg, V * 12), dtype=torch.complex128, device="cuda")

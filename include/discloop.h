@@ -59,7 +59,11 @@ typedef enum {
  * with one float scale per site and right-hand side (value = q * scale / 32767,
  * scale = the site's largest |re|,|im|), i.e. the paper's "half" precision
  * (App. A, Table A.1); arithmetic on it is FP32. */
-typedef enum { DL_F64 = 0, DL_F32 = 1, DL_F16 = 2 } dl_prec;
+typedef enum { DL_F64 = 0, DL_F32 = 1, DL_F16 = 2, DL_F64_IEEE = 5 } dl_prec;
+/* DL_F64 runs as double-float arithmetic (two floats per value, ~48 significant bits,
+ * relative rounding ~1e-14) because GB300 executes IEEE binary64 at a small fraction of
+ * its FP32 rate; DL_F64_IEEE requests IEEE binary64 kernels (dl_apply, dl_solve), e.g. for
+ * a plain FP64 baseline. */
 typedef enum { DL_C128 = 0, DL_C64 = 1 } dl_dtype;              /* natural field element type */
 
 /* Operators applied by dl_apply (natural full-lattice fields in and out). */
@@ -327,6 +331,9 @@ dl_status dl_nn_set_weights(dl_nn* nn, const float* host_w);   /* host complex64
 dl_status dl_nn_get_weights(dl_nn* nn, float* host_w);
 /* out_k = N(in_k) for n natural full-lattice fields (device, dtype). */
 dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype);
+/* out_k = N^+(in_k), the adjoint map (conjugate weights, adjoint spin factors and
+ * transports, layers in reverse order). */
+dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int dtype);
 /* Loss sum_k |N(eta_k) - s_k|^2 / |s_k|^2 over n pairs (device natural fields)
  * and its gradient with respect to conj(W) times 2 (host complex64, weight
  * layout); either output may be NULL. */
@@ -347,17 +354,23 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* params, int n_pairs, 
                       const void* s, int dtype, double* loss_hist);
 
 /* Flexible GCR (Eisenstat, Elman & Schultz 1983; flexible preconditioning as
- * in Saad 1993) on the full operator M_f, right-preconditioned by the network
- * (or by the identity when nn is NULL): FP32 inner cycles of at most `restart`
- * directions, each started from the FP64 true residual b - M x and stopped at
- * inner_tol relative to it; the FP64 solution is updated after every cycle
- * until ||b - M x|| <= tol ||b||. */
+ * in Saad 1993) on the full operator M_f (or its normal operator), preconditioned
+ * by the network (or by the identity when nn is NULL): FP32 inner cycles of at
+ * most `restart` directions, each started from the FP64 true residual b - M x and
+ * stopped at inner_tol relative to its start; the FP64 solution is updated after
+ * every cycle until ||b - M x|| <= tol ||b||.  The full operator's spectrum can
+ * surround the origin near the critical hopping parameter, where restarted GCR on
+ * M stagnates; the normal mode cannot stagnate. */
 typedef struct {
   double tol;        /* true relative residual bound */
   int max_iter;      /* inner iterations per right-hand side */
   int restart;       /* directions per inner cycle, 1..256 (two FP32 full-lattice fields each) */
   double inner_tol;  /* relative residual reduction per inner cycle */
   int flavour;       /* +1 (u) or -1 (d) */
+  int normal;        /* 0: GCR on M, right-preconditioned by N.  1: GCR on the normal
+                        operator M^+ M (Hermitian positive definite), preconditioned by
+                        N N^+ (N^+ by the network's adjoint kernels), the inner right-hand
+                        side M^+ r; the outer FP64 residual is b - M x in both modes */
 } dl_fgcr_params;
 
 typedef struct {

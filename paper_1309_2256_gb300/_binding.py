@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdiscloop.so")
 
 DL_OK, DL_ERR_ARG, DL_ERR_CUDA, DL_ERR_OOM, DL_ERR_STATE = 0, -1, -2, -3, -4
 DL_NOT_CONVERGED, DL_BREAKDOWN = 1, 3
-DL_F64, DL_F32, DL_F16, DL_BF16 = 0, 1, 2, 3
+DL_F64, DL_F32, DL_F16, DL_BF16, DL_F64_IEEE = 0, 1, 2, 3, 5
 DL_C128, DL_C64 = 0, 1
 (DL_OP_M, DL_OP_MDAG, DL_OP_HOP, DL_OP_MHAT, DL_OP_MHAT_DAG, DL_OP_PREP, DL_OP_RECON, DL_OP_BH) = range(8)
 DL_EST_STANDARD, DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE = range(4)
@@ -69,7 +69,7 @@ class dl_nn_train_params(C.Structure):
 
 class dl_fgcr_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("restart", C.c_int), ("inner_tol", C.c_double),
-                ("flavour", C.c_int)]
+                ("flavour", C.c_int), ("normal", C.c_int)]
 
 
 class dl_fgcr_stats(C.Structure):
@@ -113,6 +113,7 @@ _SIGS = {
     "dl_nn_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dl_nn_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dl_nn_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "dl_nn_apply_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "dl_nn_loss_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dl_nn_train": (C.c_int, [C.c_void_p, C.POINTER(dl_nn_train_params), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                               C.c_void_p]),
@@ -317,6 +318,10 @@ def dl_nn_get_weights(nn):
 
 def dl_nn_apply(nn, n, inp, out, dtype=DL_C128):
     return _check(nn["ctx"], lib().dl_nn_apply(nn["h"], int(n), _ptr(inp), _ptr(out), int(dtype)))
+
+
+def dl_nn_apply_adjoint(nn, n, inp, out, dtype=DL_C128):
+    return _check(nn["ctx"], lib().dl_nn_apply_adjoint(nn["h"], int(n), _ptr(inp), _ptr(out), int(dtype)))
 
 
 def dl_nn_loss_grad(nn, n, eta, s, dtype=DL_C128):

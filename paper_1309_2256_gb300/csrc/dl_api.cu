@@ -564,6 +564,9 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     std::vector<double> rr;
     if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) return s;
     CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
+    // 16-bit search directions lose conjugacy over several decades: every reliable
+    // update restarts them from the true residual (p = r); FP32 ones are kept
+    if (lo == P16) CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), c->upd, c->st));
     {
       std::vector<int> rmask(n, 0);
       bool any_restart = false;
@@ -753,7 +756,7 @@ dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int w
   const size_t nG1 = (size_t)ncomp * L.T * L.Z * L.Y * NX * npad;
   const size_t nG2 = (size_t)ncomp * L.T * L.Z * NY * NX * npad;
   const size_t nG3 = (size_t)ncomp * L.T * NZ * NY * NX * npad;
-  const size_t nph = 4096;
+  const size_t nph = 17 * 256 + 64;  // phase tables (x: up to 17 momenta x 256 sites of 16-byte pairs)
   if ((s = ensure_scratch(c, sizeof(double2) * (nW + nG1 + nG2 + nG3 + nph))) != DL_OK) return s;
   double2* W = (double2*)c->scratch;
   double2* G1 = W + nW;
@@ -765,7 +768,8 @@ dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int w
   const int fp32 = !fused ? 0 : (prec == P32 ? 1 : (prec == PDF ? 2 : 0));
   if (fused) {
     CK(dl::contract_x(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
-                      eta_o ? eta_o->ref() : NOF, prec == PDF ? c->gdf : c->g64, c->g32, c->rec32, mx, G1, c->st));
+                      eta_o ? eta_o->ref() : NOF, prec == PDF ? c->gdf : c->g64, c->g32, c->rec32, mx, ph, G1,
+                      c->st));
   } else {
     CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
                           eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
@@ -1007,7 +1011,7 @@ dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, voi
 dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux, void* out, int dtype) {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
-  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec < 0 || prec > 2 ||
+  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec_rank(prec) < 0 ||
       (dtype != DL_C128 && dtype != DL_C64))
     return fail(c, DL_ERR_ARG, "dl_apply: bad argument");
   if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");
@@ -1090,9 +1094,9 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!src || !sol || !prm || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64))
     return fail(c, DL_ERR_ARG, "dl_solve: bad argument");
-  if (!(prm->prec_hi == DL_F64 || prm->prec_hi == DL_F32) || prm->prec_lo < 0 || prm->prec_lo > 2 ||
-      prm->prec_lo < prm->prec_hi || !(prm->tol > 0.0) || prm->max_iter < 1 || (prm->flavour != 1 && prm->flavour != -1) ||
-      prm->delta < 0.0 || prm->delta >= 1.0)
+  if (prec_rank(prm->prec_hi) < 0 || prec_rank(prm->prec_hi) > 1 || prec_rank(prm->prec_lo) < prec_rank(prm->prec_hi) ||
+      !(prm->tol > 0.0) || prm->max_iter < 1 || (prm->flavour != 1 && prm->flavour != -1) || prm->delta < 0.0 ||
+      prm->delta >= 1.0)
     return fail(c, DL_ERR_ARG, "dl_solve: bad parameters");
   if ((s = enter(c)) != DL_OK) return s;
   dl_solve_params sp = *prm;
@@ -1599,7 +1603,7 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
                                       void* out, int dtype) {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
-  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec < 0 || prec > 2 ||
+  if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec_rank(prec) < 0 ||
       (dtype != DL_C128 && dtype != DL_C64) || op < DL_OP_M || op > DL_OP_BH)
     return fail(c, DL_ERR_ARG, "dl_apply_noalloc: bad argument");
   if (op == DL_OP_RECON && !aux) return fail(c, DL_ERR_ARG, "DL_OP_RECON needs aux");

@@ -359,7 +359,7 @@ cudaError_t copy(const Batch& Bin, int pd, int ps, FieldRef dst, FieldRef src, c
   if (!g) return cudaSuccess;
 #define CP(a, b) if (pd == a && ps == b) { DL_COUNT(); copy_kernel<a, b><<<g, 256, 0, st>>>(B, dst, src, mask); return cudaGetLastError(); }
   CP(P64, P64) CP(P64, P32) CP(P64, P16) CP(P32, P64) CP(P32, P32) CP(P32, P16) CP(P16, P64) CP(P16, P32) CP(P16, P16)
-  CP(PBF, P64) CP(P64, PBF) CP(PBF, P32) CP(P32, PBF)
+  CP(PBF, P64) CP(P64, PBF) CP(PBF, P32) CP(P32, PBF) CP(PBF, PBF)
   CP(PDF, PDF) CP(PDF, P64) CP(P64, PDF) CP(PDF, P32) CP(P32, PDF) CP(PDF, P16) CP(P16, PDF)
 #undef CP
   return cudaErrorInvalidValue;

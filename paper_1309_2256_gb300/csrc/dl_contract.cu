@@ -183,28 +183,42 @@ struct RPair {
   R x, y;
 };
 
+#define DL_NXMAX 17  // x momenta per row: 2 floor(sqrt(P)) + 1 for |n|^2 <= P <= 64
+
+// Phase table of the x DFT: pht[kx][x] = exp(-2 pi i (kx - mx) x / X) in R.
+template <typename R>
+__global__ void phase_table_kernel(int X, int mx, RPair<R>* pht) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int NX = 2 * mx + 1;
+  if (e >= NX * X) return;
+  const int kx = e / X, xx = e % X;
+  int q = ((kx - mx) * xx) % X;
+  if (q < 0) q += X;
+  double sn, cn;
+  sincospi(2.0 * (double)q / (double)X, &sn, &cn);
+  pht[e].x = (R)cn;
+  pht[e].y = (R)(-sn);
+}
+
 template <int P, int MODE, bool DERIV, typename R, int G>
 __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                                                            FieldRef eta_o, const void* __restrict__ gbase, int mx,
-                                                           int cwlog, RPair<R>* __restrict__ G1) {
+                                                           int cwlog, const RPair<R>* __restrict__ phx,
+                                                           RPair<R>* __restrict__ G1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const LatDesc& L = B.lat[0];
   const int lg = L.lognpad, npad = 1 << lg;
   const int cw = 1 << cwlog;                     // columns handled by this CTA
   const int NX = 2 * mx + 1;
   typedef RPair<R> cr;
-  cr* cs = (cr*)smem_raw;                        // [16][X][cw]
-  cr* ph = cs + 16 * L.X * cw;                   // [X]
+  cr* cs = (cr*)smem_raw;                        // [16][X][cw] site components
+  cr* pht = cs + 16 * L.X * cw;                  // [NX][X] phases
+  cr* part = pht + NX * L.X;                     // [2 halves][16][NX][cw] partial DFT sums
   const int row = blockIdx.x;                    // (t * Z + z) * Y + y
   const int y = row % L.Y, z = (row / L.Y) % L.Z, t = row / (L.Y * L.Z);
   const int x = threadIdx.x >> cwlog, cl = threadIdx.x & (cw - 1);
   const int col = blockIdx.y * cw + cl;
-  if (threadIdx.x < L.X) {
-    double sn, cn;
-    sincospi(2.0 * (double)threadIdx.x / (double)L.X, &sn, &cn);
-    ph[threadIdx.x].x = (R)cn;
-    ph[threadIdx.x].y = (R)(-sn);
-  }
+  for (int e = threadIdx.x; e < NX * L.X; e += blockDim.x) pht[e] = phx[e];
   const long long nitems = (long long)L.Vh << lg;
   const int lex = lex_of(L, x, y, z, t);
   const int p = (x + y + z + t) & 1;
@@ -300,24 +314,38 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
       cs[(k * L.X + x) * cw + cl].y = cim[k];
     }
     __syncthreads();
-    const int ntask = 16 * NX * cw;
-    for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    // x DFT, register-blocked: task (half of the row, component k, column cc) reads each
+    // site value once and updates all NX momenta; the two halves are added in a fixed order
+    const int half = (L.X + 1) >> 1;
+    for (int task = threadIdx.x; task < 32 * cw; task += blockDim.x) {
       const int cc = task & (cw - 1);
-      const int kx = (task >> cwlog) % NX;
-      const int k = (task >> cwlog) / NX;
-      int n = kx - mx;
-      n = ((n % L.X) + L.X) % L.X;
-      R re = 0, im = 0;
-      int q = 0;
-      for (int xx = 0; xx < L.X; ++xx) {
+      const int k = (task >> cwlog) & 15;
+      const int xh = task >> (cwlog + 4);
+      const int x0 = xh * half, x1 = (x0 + half < L.X) ? x0 + half : L.X;
+      R ar[DL_NXMAX], ai[DL_NXMAX];
+#pragma unroll
+      for (int kx = 0; kx < DL_NXMAX; ++kx) ar[kx] = ai[kx] = 0;
+      for (int xx = x0; xx < x1; ++xx) {
         const cr v = cs[(k * L.X + xx) * cw + cc];
-        const cr w = ph[q];
-        re += v.x * w.x - v.y * w.y;
-        im += v.x * w.y + v.y * w.x;
-        q += n;
-        if (q >= L.X) q -= L.X;
+#pragma unroll
+        for (int kx = 0; kx < DL_NXMAX; ++kx)
+          if (kx < NX) {
+            const cr w = pht[kx * L.X + xx];
+            ar[kx] += v.x * w.x - v.y * w.y;
+            ai[kx] += v.x * w.y + v.y * w.x;
+          }
       }
-      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] = cr{re, im};
+#pragma unroll
+      for (int kx = 0; kx < DL_NXMAX; ++kx)
+        if (kx < NX) part[((xh * 16 + k) * NX + kx) * cw + cc] = cr{ar[kx], ai[kx]};
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 16 * NX * cw; e += blockDim.x) {
+      const int cc = e & (cw - 1);
+      const int kx = (e >> cwlog) % NX;
+      const int k = (e >> cwlog) / NX;
+      const cr a = part[(k * NX + kx) * cw + cc], b = part[((16 + k) * NX + kx) * cw + cc];
+      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] = cr{a.x + b.x, a.y + b.y};
     }
   }
 }
@@ -609,7 +637,7 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
 }
 
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
-                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* G1,
+                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* phx, double2* G1,
                        cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   const int npad = 1 << L.lognpad;
@@ -617,15 +645,20 @@ cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, Field
   while (cwlog > 0 && (L.X << cwlog) > 256) --cwlog;  // X * cw <= 256 threads per CTA
   const int threads = L.X << cwlog;
   if (threads > 256 || threads < 1) return cudaErrorInvalidValue;
-  if (prec != P64 && rec32 != 12 && rec32 != 8) return cudaErrorInvalidValue;
+  if (prec == P32 && rec32 != 12 && rec32 != 8) return cudaErrorInvalidValue;
+  const int NX = 2 * mx + 1;
+  if (NX > DL_NXMAX) return cudaErrorInvalidValue;
   const dim3 grid(L.T * L.Z * L.Y, npad >> cwlog);
 #define CXK(PR, MD, DV, R, G, GB)                                                                                   \
   {                                                                                                                \
-    const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + L.X) * 2 * sizeof(R);                                   \
+    const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 32 * NX * (1 << cwlog)) * 2 * sizeof(R);     \
+    if (smem > 200000) return cudaErrorInvalidValue;                                                               \
+    DL_COUNT();                                                                                                    \
+    phase_table_kernel<R><<<(NX * L.X + 255) / 256, 256, 0, st>>>(L.X, mx, (RPair<R>*)phx);                        \
     cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
     DL_COUNT();                                                                                                    \
     contract_x_kernel<PR, MD, DV, R, G><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, GB, mx, cwlog,      \
-                                                                      (RPair<R>*)G1);                              \
+                                                                      (const RPair<R>*)phx, (RPair<R>*)G1);        \
     return cudaGetLastError();                                                                                     \
   }
 #define CX(PR, MD)                                                                                                  \

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : DL_
 
 // Direct mapping (npad < 4): every thread computes its own neighbours and links.
 template <int P, int G, int EPI>
-__global__ void __launch_bounds__(256) dslash_kernel(Batch B, int out_parity, float sgn_fwd, FieldRef in, FieldRef aux,
+__global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : 1) dslash_kernel(Batch B, int out_parity, float sgn_fwd, FieldRef in, FieldRef aux,
                                                      FieldRef out, const void* __restrict__ gbase, EpiSet ep,
                                                      const int* __restrict__ active, double* __restrict__ partial,
                                                      FieldRef cr, FieldRef cy, FieldRef cp,

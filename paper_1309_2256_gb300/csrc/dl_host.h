@@ -34,7 +34,13 @@ inline size_t chunk_bytes(int prec) { return (prec == P64 || prec == PDF) ? 192 
 
 // The API's FP64 precision as the kernels run it: double-float arithmetic on
 // FP32 units (dl_df.cuh), since GB300's FP64 rate is a small fraction of FP32.
-inline int internal_prec(int api_prec) { return api_prec == DL_F64 ? PDF : api_prec; }
+inline int internal_prec(int api_prec) {
+  return api_prec == DL_F64 ? PDF : (api_prec == DL_F64_IEEE ? P64 : api_prec);
+}
+// 0 for both FP64 forms, 1 FP32, 2 16-bit; -1 for anything else
+inline int prec_rank(int api_prec) {
+  return (api_prec == DL_F64 || api_prec == DL_F64_IEEE) ? 0 : (api_prec == DL_F32 ? 1 : (api_prec == DL_F16 ? 2 : -1));
+}
 
 struct LatInfo {
   int dims[4];

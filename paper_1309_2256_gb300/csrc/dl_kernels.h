@@ -53,7 +53,7 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
 // G1 (and the DFT passes' buffers) hold float pairs for P32, double-float pairs for PDF
 // and double pairs for P64; dft_pass / contract_finalize take the kind as fp32 = 1 / 2 / 0
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
-                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* G1,
+                       FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* phx, double2* G1,
                        cudaStream_t st);
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
                               const double2* G3, int fp32, double pre_re, double pre_im, double2* out, int accumulate,

@@ -89,6 +89,18 @@ dl_status backward(dl_nn* nn, const Acts& X, const Acts& G) {
   return DL_OK;
 }
 
+// G[0] = N^+ G[nl]: the adjoint of every layer (the input-gradient kernels) from the last to the first.
+dl_status adjoint(dl_nn* nn, const Acts& G) {
+  dl_ctx* c = nn->c;
+  const LatDesc L = make_batch(c, 1).lat[0];
+  for (int l = nn->nl - 1; l >= 0; --l)
+    for (int p = 0; p < 2; ++p)
+      CK(dl::nn_backward_x(L, nn->act, c->rec32, p, G.e[l + 1]->ref(), G.o[l + 1]->ref(),
+                           p ? G.o[l]->ref() : G.e[l]->ref(), c->g32, nn->W + nn->woff[l], nn->ci[l], nn->co[l],
+                           lg_in(nn, l), lg_out(nn, l), c->st));
+  return DL_OK;
+}
+
 dl_status zero_wpart(dl_nn* nn) {
   dl_ctx* c = nn->c;
   CK(cudaMemsetAsync(nn->wpart, 0, sizeof(float2) * nn->npart * nn->slots, c->st));
@@ -317,6 +329,27 @@ dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype) {
   return leave(c);
 }
 
+dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int dtype) {
+  if (!valid_nn(nn)) return DL_ERR_ARG;
+  dl_ctx* c = nn->c;
+  if (!in || !out || n < 1 || (dtype != DL_C128 && dtype != DL_C64))
+    return fail(c, DL_ERR_ARG, "dl_nn_apply_adjoint: bad argument");
+  dl_status s;
+  if ((s = enter(c)) != DL_OK) return s;
+  Acts G;
+  if ((s = get_acts(nn, "g", 0, G)) != DL_OK) return s;
+  const Batch B1 = make_batch(c, 1);
+  for (int k = 0; k < n; ++k) {
+    const size_t off = (size_t)k * 2 * c->Vh * site_bytes(dtype);
+    for (int p = 0; p < 2; ++p)
+      CK(dl::pack(B1, nn->act, p, p ? G.o[nn->nl]->ref() : G.e[nn->nl]->ref(), (const char*)in + off, dtype, c->st));
+    if ((s = adjoint(nn, G)) != DL_OK) return s;
+    for (int p = 0; p < 2; ++p)
+      CK(dl::unpack(B1, nn->act, p, (char*)out + off, p ? G.o[0]->ref() : G.e[0]->ref(), dtype, c->st));
+  }
+  return leave(c);
+}
+
 dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int dtype, double* loss, float* grad) {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
@@ -425,22 +458,40 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
         (s = ensure_field(c, "fg_we" + k, P32, B1, &we[j])) || (s = ensure_field(c, "fg_wo" + k, P32, B1, &wo[j])))
       return s;
   }
-  Acts X;
+  const bool normal = prm->normal != 0;
+  Field *u3e, *u3o, *v3e, *v3o;  // normal mode: normalised true residual, and M z before M^+
+  if ((s = ensure_field(c, "fg_u3e", P32, B1, &u3e)) || (s = ensure_field(c, "fg_u3o", P32, B1, &u3o)) ||
+      (s = ensure_field(c, "fg_v3e", P32, B1, &v3e)) || (s = ensure_field(c, "fg_v3o", P32, B1, &v3o)))
+    return s;
+  Acts X, G;
   if (nn && (s = get_acts(nn, "x", 0, X)) != DL_OK) return s;
+  if (nn && normal && (s = get_acts(nn, "g", 0, G)) != DL_OK) return s;
   void* p;
   if ((s = ensure_buf(c, "fg_scal", sizeof(double) * 2, &p)) != DL_OK) return s;
   double* dsc = (double*)p;
   GaugeSet g{c->g64, c->g32, c->g16};
-  const EpiSet E = epiB(B1, CK_MK, 0, 0, 1, prm->flavour);  // out_p = R_f in_p - kappa D in_{1-p}
+  const EpiSet E = epiB(B1, CK_MK, 0, 0, 1, prm->flavour);    // out_p = R_f in_p - kappa D in_{1-p}
+  const EpiSet Ed = epiB(B1, CK_MK, 0, 0, 1, -prm->flavour);  // the same for M^+ (dagger projectors, -mu)
   long long nop = 0, nnn = 0;
-  auto applyM = [&](int prec, Field* ie, Field* io, Field* oe, Field* oo) -> dl_status {
+  auto applyMd = [&](int prec, bool dag, Field* ie, Field* io, Field* oe, Field* oo) -> dl_status {
     const int gr = grec_of(c, prec);
-    CK(dl::dslash(B1, prec, gr, EPI_AUX, false, 0, io->ref(), ie->ref(), oe->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
+    const EpiSet& EE = dag ? Ed : E;
+    CK(dl::dslash(B1, prec, gr, EPI_AUX, dag, 0, io->ref(), ie->ref(), oe->ref(), g, EE, nullptr, nullptr, NOF, NOF, NOF,
                   nullptr, c->st));
-    CK(dl::dslash(B1, prec, gr, EPI_AUX, false, 1, ie->ref(), io->ref(), oo->ref(), g, E, nullptr, nullptr, NOF, NOF, NOF,
+    CK(dl::dslash(B1, prec, gr, EPI_AUX, dag, 1, ie->ref(), io->ref(), oo->ref(), g, EE, nullptr, nullptr, NOF, NOF, NOF,
                   nullptr, c->st));
     ++nop;
     return DL_OK;
+  };
+  auto applyM = [&](int prec, Field* ie, Field* io, Field* oe, Field* oo) -> dl_status {
+    return applyMd(prec, false, ie, io, oe, oo);
+  };
+  // the inner operator: M, or M^+ M in normal mode
+  auto applyA = [&](Field* ie, Field* io, Field* oe, Field* oo) -> dl_status {
+    if (!normal) return applyM(P32, ie, io, oe, oo);
+    dl_status s2 = applyMd(P32, false, ie, io, v3e, v3o);
+    if (s2 != DL_OK) return s2;
+    return applyMd(P32, true, v3e, v3o, oe, oo);
   };
   auto dot = [&](int prec, Field* ae, Field* ao, Field* b2e, Field* b2o, double& dr, double& di) -> dl_status {
     CK(dl::pdot(B1, prec, ae->ref(), ao->ref(), b2e->ref(), b2o->ref(), c->partial, dsc, c->st));
@@ -462,8 +513,17 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
       CK(dl::copy(B1, P32, P32, oo->ref(), io->ref(), nullptr, c->st));
       return DL_OK;
     }
-    CK(dl::copy(B1, nn->act, P32, X.e[0]->ref(), ie->ref(), nullptr, c->st));
-    CK(dl::copy(B1, nn->act, P32, X.o[0]->ref(), io->ref(), nullptr, c->st));
+    if (normal) {  // P = N N^+ (symmetric positive definite for an invertible N)
+      CK(dl::copy(B1, nn->act, P32, G.e[nn->nl]->ref(), ie->ref(), nullptr, c->st));
+      CK(dl::copy(B1, nn->act, P32, G.o[nn->nl]->ref(), io->ref(), nullptr, c->st));
+      dl_status s3 = adjoint(nn, G);
+      if (s3 != DL_OK) return s3;
+      CK(dl::copy(B1, nn->act, nn->act, X.e[0]->ref(), G.e[0]->ref(), nullptr, c->st));
+      CK(dl::copy(B1, nn->act, nn->act, X.o[0]->ref(), G.o[0]->ref(), nullptr, c->st));
+    } else {
+      CK(dl::copy(B1, nn->act, P32, X.e[0]->ref(), ie->ref(), nullptr, c->st));
+      CK(dl::copy(B1, nn->act, P32, X.o[0]->ref(), io->ref(), nullptr, c->st));
+    }
     dl_status s2 = forward(nn, X);
     if (s2 != DL_OK) return s2;
     CK(dl::copy(B1, P32, nn->act, oe->ref(), X.e[nn->nl]->ref(), nullptr, c->st));
@@ -489,15 +549,23 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
     double rn = bn;
     while (bn > 0.0 && rn > prm->tol * bn && iters < prm->max_iter) {
       ++cycles;
-      // inner FP32 cycle on the normalised residual
-      CK(dl::copy(B1, P32, P64, r3e->ref(), re->ref(), nullptr, c->st));
-      CK(dl::copy(B1, P32, P64, r3o->ref(), ro->ref(), nullptr, c->st));
-      if ((s = axpy(P32, 1.0 / rn - 1.0, 0.0, r3e, r3o, r3e, r3o)) != DL_OK) return s;
+      // inner FP32 cycle on the normalised residual (normal mode: on M^+ of it)
+      Field* ue = normal ? u3e : r3e;
+      Field* uo = normal ? u3o : r3o;
+      CK(dl::copy(B1, P32, P64, ue->ref(), re->ref(), nullptr, c->st));
+      CK(dl::copy(B1, P32, P64, uo->ref(), ro->ref(), nullptr, c->st));
+      if ((s = axpy(P32, 1.0 / rn - 1.0, 0.0, ue, uo, ue, uo)) != DL_OK) return s;
+      double rho0 = 1.0;
+      if (normal) {
+        if ((s = applyMd(P32, true, u3e, u3o, r3e, r3o)) != DL_OK) return s;
+        if ((s = dot(P32, r3e, r3o, r3e, r3o, dr, di)) != DL_OK) return s;
+        rho0 = std::sqrt(std::max(dr, 0.0));
+      }
       CK(dl::zero(B1, P32, e3e->ref(), nullptr, c->st));
       CK(dl::zero(B1, P32, e3o->ref(), nullptr, c->st));
       for (int j = 0; j < m && iters < prm->max_iter; ++j) {
         if ((s = precond(r3e, r3o, ze[j], zo[j])) != DL_OK) return s;
-        if ((s = applyM(P32, ze[j], zo[j], we[j], wo[j])) != DL_OK) return s;
+        if ((s = applyA(ze[j], zo[j], we[j], wo[j])) != DL_OK) return s;
         for (int i = 0; i < j; ++i) {  // modified Gram-Schmidt against the unit directions w_i
           if ((s = dot(P32, we[i], wo[i], we[j], wo[j], dr, di)) != DL_OK) return s;
           if ((s = axpy(P32, -dr, -di, we[i], wo[i], we[j], wo[j])) != DL_OK) return s;
@@ -515,7 +583,7 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
         ++iters;
         if ((s = dot(P32, r3e, r3o, r3e, r3o, dr, di)) != DL_OK) return s;
         const double rho = std::sqrt(std::max(dr, 0.0));
-        if (rho <= prm->inner_tol || rho * rn <= 0.5 * prm->tol * bn) break;
+        if (rho <= prm->inner_tol * rho0 || (!normal && rho * rn <= 0.5 * prm->tol * bn)) break;
       }
       // x += |r| e; r = b - M x in FP64
       CK(dl::copy(B1, P64, P32, te->ref(), e3e->ref(), nullptr, c->st));

@@ -85,6 +85,32 @@ def test_forward_matches_oracle(dl, act, tol, n_layers, c):
         assert np.abs(got[r] - ref).max() <= tol * np.abs(ref).max(), r
 
 
+def test_adjoint_matches_oracle(dl):
+    """N^+ y from the input-gradient kernels against the oracle's layer adjoints (FP32)."""
+    dims = (4, 4, 4, 4)
+    n_layers, c = 4, 16
+    links = synth.gauge_links(dims, 0.4, 316)
+    w = synth.network_weights(n_layers, c, 63, scale=0.6, identity=0.5)
+    y = synth.gaussian_spinors(dims, 1, 64)
+    ctx = _ctx(dl, dims, links, 0.16, 0.01)
+    try:
+        nn = dl.dl_nn_create(ctx, n_layers, c, dl.DL_F32)
+        dl.dl_nn_set_weights(nn, w)
+        out = torch.zeros(y.size, dtype=torch.complex128, device="cuda")
+        dl.dl_nn_apply_adjoint(nn, 1, _dev(y), out)
+        got = out.cpu().numpy().reshape(y.shape)
+        dl.dl_nn_destroy(nn)
+    finally:
+        dl.dl_destroy(ctx)
+    ws = _to_oracle(w, n_layers, c)
+    g = y  # [1, ...] one channel at the output
+    for li in range(n_layers - 1, -1, -1):
+        ci = 1 if li == 0 else c
+        x0 = np.zeros((ci,) + dims[::-1] + (4, 3), dtype=np.complex128)  # the input only enters gw
+        _, g = network.layer_backward(links, ws[li], x0, g)
+    assert np.abs(got - g).max() <= 2e-6 * np.abs(g).max()
+
+
 def test_loss_and_gradients_match_oracle(dl):
     """Loss and every weight gradient (2 dL/d conj W) of three pairs, FP32 activations."""
     dims = (4, 4, 2, 4)
@@ -142,8 +168,10 @@ def test_gauge_equivariance_on_gpu(dl):
     assert np.abs(outs[1] - ref).max() <= 3e-6 * np.abs(ref).max()
 
 
-def test_fgcr_without_network_matches_dense(dl):
-    """Flexible GCR with the identity preconditioner reaches 1e-10; solution vs dense LU."""
+@pytest.mark.parametrize("normal", [0, 1])
+def test_fgcr_without_network_matches_dense(dl, normal):
+    """Flexible GCR with the identity preconditioner (on M, or on M^+ M) reaches 1e-10;
+    solution vs dense LU."""
     dims = (4, 4, 4, 4)
     kappa, amu = 0.16, 0.01
     links = synth.gauge_links(dims, 0.3, 1000)
@@ -151,7 +179,7 @@ def test_fgcr_without_network_matches_dense(dl):
     ctx = _ctx(dl, dims, links, kappa, amu)
     try:
         sol = torch.zeros(eta.size, dtype=torch.complex128, device="cuda")
-        prm = dl.dl_fgcr_params(tol=1e-10, max_iter=5000, restart=16, inner_tol=1e-5, flavour=1)
+        prm = dl.dl_fgcr_params(tol=1e-10, max_iter=5000, restart=16, inner_tol=1e-5, flavour=1, normal=normal)
         st, stats = dl.dl_fgcr_solve(ctx, None, prm, 3, _dev(eta), sol)
         assert st == 0
         got = sol.cpu().numpy().reshape(eta.shape)
@@ -201,19 +229,21 @@ def test_training_reduces_loss(trained):
     assert h[-20:].mean() < 0.7 * h[:20].mean(), (h[:20].mean(), h[-20:].mean())
 
 
-def test_trained_network_preconditions_fgcr(trained):
+@pytest.mark.parametrize("normal", [0, 1])
+def test_trained_network_preconditions_fgcr(trained, normal):
     """Fresh noise: FGCR to 1e-10 with the trained network needs fewer iterations than
-    without it (same restart length); the solutions satisfy M s = eta to 1e-10 (oracle)."""
+    without it (same restart length; on M the unpreconditioned solve may stagnate, on
+    M^+ M both converge); the solutions satisfy M s = eta to 1e-10 (oracle)."""
     dl, ctx, nn, V = trained["dl"], trained["ctx"], trained["nn"], trained["V"]
     n = 4
     eta = torch.zeros(n * V * 12, dtype=torch.complex128, device="cuda")
     dl.dl_noise_z4(ctx, 4048, 0, n, eta)
-    prm = dl.dl_fgcr_params(tol=1e-10, max_iter=3000, restart=16, inner_tol=1e-4, flavour=1)
+    prm = dl.dl_fgcr_params(tol=1e-10, max_iter=3000, restart=32, inner_tol=1e-4, flavour=1, normal=normal)
     out = {}
     for name, net in (("plain", None), ("net", nn)):
         sol = torch.zeros_like(eta)
         st, stats = dl.dl_fgcr_solve(ctx, net, prm, n, eta, sol)
-        assert st == 0 or (name == "plain" and st == dl.DL_NOT_CONVERGED)
+        assert st == 0 or (name == "plain" and not normal and st == dl.DL_NOT_CONVERGED)
         out[name] = (np.array(stats.iters[:n]), sol.cpu().numpy())
     assert out["net"][0].mean() < 0.8 * out["plain"][0].mean(), (out["net"][0], out["plain"][0])
     e = eta.cpu().numpy().reshape((n,) + trained["dims"][::-1] + (4, 3))
