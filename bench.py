@@ -449,16 +449,20 @@ def learned_case(args):
     # inference: one network application, timed with events on the current stream
     one_in = eta[:1].clone()
     one_out = torch.empty_like(one_in)
-    for _ in range(3):
-        dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 10
-    e0.record()
-    for _ in range(reps):
-        dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_apply = e0.elapsed_time(e1) / reps
+    ms_by = {}
+    for tc in (0, 1):  # CUDA-core and tensor-core channel mixing
+        dl.dl_nn_set_tensor_cores(nn, tc)
+        for _ in range(3):
+            dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            dl.dl_nn_apply(nn, 1, one_in, one_out, dl.DL_C64)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_by["tensor_cores" if tc else "cuda_cores"] = e0.elapsed_time(e1) / reps
+    ms_apply = ms_by["tensor_cores"]
     # flops of one application, per site and layer: channel mixing, 9 terms x 12 components x 2
     # complex multiply-adds (8 flops each) per (output, input) channel pair; transports, 8 links x
     # 4 spins x 9 complex multiply-adds per input channel
@@ -467,7 +471,7 @@ def learned_case(args):
         ci = 1 if l == 0 else 16
         co = 1 if l == 3 else 16
         flops += V * (co * ci * 9 * 12 * 2 * 8 + ci * 8 * 4 * 3 * 3 * 8)
-    out["apply"] = {"ms": ms_apply, "tflops": flops / ms_apply / 1e9, "flops_per_apply": flops}
+    out["apply"] = {"ms": ms_apply, "tflops": flops / ms_apply / 1e9, "flops_per_apply": flops, "ms_by_backend": ms_by}
     progress(f"one application {ms_apply:.2f} ms")
     # fresh noise: FGCR with / without the network, plain mixed-precision CG
     fresh = torch.empty((args.fresh, V * 12), dtype=torch.complex128, device="cuda")

@@ -110,6 +110,7 @@ _SIGS = {
     "dl_nn_create": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "dl_nn_destroy": (None, [C.c_void_p]),
     "dl_nn_weight_count": (C.c_longlong, [C.c_void_p]),
+    "dl_nn_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int]),
     "dl_nn_set_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dl_nn_get_weights": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dl_nn_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
@@ -302,6 +303,10 @@ def dl_nn_destroy(nn):
 
 def dl_nn_weight_count(nn):
     return int(lib().dl_nn_weight_count(nn["h"]))
+
+
+def dl_nn_set_tensor_cores(nn, enable):
+    return _check(nn["ctx"], lib().dl_nn_set_tensor_cores(nn["h"], int(enable)))
 
 
 def dl_nn_set_weights(nn, w):

@@ -200,7 +200,9 @@ __global__ void phase_table_kernel(int X, int mx, RPair<R>* pht) {
   pht[e].y = (R)(-sn);
 }
 
-template <int P, int MODE, bool DERIV, typename R, int G>
+// MXT >= 0: the x-momentum extent mx is the compile-time MXT (no predicated
+// iterations in the register-blocked DFT); MXT = -1: any mx <= 8.
+template <int P, int MODE, bool DERIV, typename R, int G, int MXT>
 __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                                                            FieldRef eta_o, const void* __restrict__ gbase, int mx,
                                                            int cwlog, const RPair<R>* __restrict__ phx,
@@ -322,22 +324,23 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
       const int k = (task >> cwlog) & 15;
       const int xh = task >> (cwlog + 4);
       const int x0 = xh * half, x1 = (x0 + half < L.X) ? x0 + half : L.X;
-      R ar[DL_NXMAX], ai[DL_NXMAX];
+      constexpr int NXC = MXT >= 0 ? 2 * MXT + 1 : DL_NXMAX;
+      R ar[NXC], ai[NXC];
 #pragma unroll
-      for (int kx = 0; kx < DL_NXMAX; ++kx) ar[kx] = ai[kx] = 0;
+      for (int kx = 0; kx < NXC; ++kx) ar[kx] = ai[kx] = 0;
       for (int xx = x0; xx < x1; ++xx) {
         const cr v = cs[(k * L.X + xx) * cw + cc];
 #pragma unroll
-        for (int kx = 0; kx < DL_NXMAX; ++kx)
-          if (kx < NX) {
+        for (int kx = 0; kx < NXC; ++kx)
+          if (MXT >= 0 || kx < NX) {
             const cr w = pht[kx * L.X + xx];
             ar[kx] += v.x * w.x - v.y * w.y;
             ai[kx] += v.x * w.y + v.y * w.x;
           }
       }
 #pragma unroll
-      for (int kx = 0; kx < DL_NXMAX; ++kx)
-        if (kx < NX) part[((xh * 16 + k) * NX + kx) * cw + cc] = cr{ar[kx], ai[kx]};
+      for (int kx = 0; kx < NXC; ++kx)
+        if (MXT >= 0 || kx < NX) part[((xh * 16 + k) * NX + kx) * cw + cc] = cr{ar[kx], ai[kx]};
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 16 * NX * cw; e += blockDim.x) {
@@ -636,6 +639,63 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
   return cudaErrorInvalidValue;
 }
 
+template <int PR, int MD, bool DV, typename R, int G, int MXT>
+cudaError_t launch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx, FieldRef s_e, FieldRef s_o,
+                      FieldRef eta_e, FieldRef eta_o, const void* gb, double2* phx, double2* G1, cudaStream_t st) {
+  const LatDesc& L = B.lat[0];
+  const int NX = 2 * mx + 1;
+  const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 32 * NX * (1 << cwlog)) * 2 * sizeof(R);
+  if (smem > 200000) return cudaErrorInvalidValue;
+  DL_COUNT();
+  phase_table_kernel<R><<<(NX * L.X + 255) / 256, 256, 0, st>>>(L.X, mx, (RPair<R>*)phx);
+  cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G, MXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+  DL_COUNT();
+  contract_x_kernel<PR, MD, DV, R, G, MXT><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gb, mx, cwlog,
+                                                                         (const RPair<R>*)phx, (RPair<R>*)G1);
+  return cudaGetLastError();
+}
+
+// One (precision, estimator, derivative) combination: its arithmetic type and gauge
+// copy, and for the FP32 local contractions of the LP pipeline a kernel per x extent.
+template <int PR, int MD, bool DV>
+cudaError_t dispatch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx, FieldRef s_e, FieldRef s_o,
+                        FieldRef eta_e, FieldRef eta_o, const void* g64, const void* g32, int rec32, double2* phx,
+                        double2* G1, cudaStream_t st) {
+#define ARGS B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o
+  if constexpr (PR == P64) {
+    return launch_cx<PR, MD, DV, double, G64R18, -1>(ARGS, g64, phx, G1, st);
+  } else if constexpr (PR == PDF) {
+    return launch_cx<PR, MD, DV, dfloat, GDF18, -1>(ARGS, g64, phx, G1, st);
+  } else {
+    if constexpr (!DV) {
+      if (rec32 == 12) {
+        switch (mx) {
+          case 0: return launch_cx<PR, MD, DV, float, G32R12, 0>(ARGS, g32, phx, G1, st);
+          case 1: return launch_cx<PR, MD, DV, float, G32R12, 1>(ARGS, g32, phx, G1, st);
+          case 2: return launch_cx<PR, MD, DV, float, G32R12, 2>(ARGS, g32, phx, G1, st);
+          case 3: return launch_cx<PR, MD, DV, float, G32R12, 3>(ARGS, g32, phx, G1, st);
+          default: break;
+        }
+      } else {
+        switch (mx) {
+          case 0: return launch_cx<PR, MD, DV, float, G32R8, 0>(ARGS, g32, phx, G1, st);
+          case 1: return launch_cx<PR, MD, DV, float, G32R8, 1>(ARGS, g32, phx, G1, st);
+          case 2: return launch_cx<PR, MD, DV, float, G32R8, 2>(ARGS, g32, phx, G1, st);
+          case 3: return launch_cx<PR, MD, DV, float, G32R8, 3>(ARGS, g32, phx, G1, st);
+          default: break;
+        }
+      }
+    }
+    if (rec32 == 12) return launch_cx<PR, MD, DV, float, G32R12, -1>(ARGS, g32, phx, G1, st);
+    return launch_cx<PR, MD, DV, float, G32R8, -1>(ARGS, g32, phx, G1, st);
+  }
+#undef ARGS
+}
+
+}  // namespace dl
+
+namespace dl {
+
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                        FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* phx, double2* G1,
                        cudaStream_t st) {
@@ -646,38 +706,18 @@ cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, Field
   const int threads = L.X << cwlog;
   if (threads > 256 || threads < 1) return cudaErrorInvalidValue;
   if (prec == P32 && rec32 != 12 && rec32 != 8) return cudaErrorInvalidValue;
-  const int NX = 2 * mx + 1;
-  if (NX > DL_NXMAX) return cudaErrorInvalidValue;
+  if (2 * mx + 1 > DL_NXMAX) return cudaErrorInvalidValue;
   const dim3 grid(L.T * L.Z * L.Y, npad >> cwlog);
-#define CXK(PR, MD, DV, R, G, GB)                                                                                   \
-  {                                                                                                                \
-    const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 32 * NX * (1 << cwlog)) * 2 * sizeof(R);     \
-    if (smem > 200000) return cudaErrorInvalidValue;                                                               \
-    DL_COUNT();                                                                                                    \
-    phase_table_kernel<R><<<(NX * L.X + 255) / 256, 256, 0, st>>>(L.X, mx, (RPair<R>*)phx);                        \
-    cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000); \
-    DL_COUNT();                                                                                                    \
-    contract_x_kernel<PR, MD, DV, R, G><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, GB, mx, cwlog,      \
-                                                                      (const RPair<R>*)phx, (RPair<R>*)G1);        \
-    return cudaGetLastError();                                                                                     \
-  }
 #define CX(PR, MD)                                                                                                  \
-  if (prec == PR && mode == MD) {                                                                                  \
-    if (PR == P64) {                                                                                               \
-      if (with_deriv) CXK(PR, MD, true, double, G64R18, g64) else CXK(PR, MD, false, double, G64R18, g64)         \
-    } else if (PR == PDF) {                                                                                        \
-      if (with_deriv) CXK(PR, MD, true, dfloat, GDF18, g64) else CXK(PR, MD, false, dfloat, GDF18, g64)           \
-    } else if (rec32 == 12) {                                                                                      \
-      if (with_deriv) CXK(PR, MD, true, float, G32R12, g32) else CXK(PR, MD, false, float, G32R12, g32)           \
-    } else {                                                                                                       \
-      if (with_deriv) CXK(PR, MD, true, float, G32R8, g32) else CXK(PR, MD, false, float, G32R8, g32)             \
-    }                                                                                                              \
-  }
+  if (prec == PR && mode == MD)                                                                                    \
+    return with_deriv ? dispatch_cx<PR, MD, true>(B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o, g64, g32,   \
+                                                  rec32, phx, G1, st)                                              \
+                      : dispatch_cx<PR, MD, false>(B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o, g64, g32,  \
+                                                   rec32, phx, G1, st);
   CX(P64, 0) CX(P64, 1) CX(P64, 2) CX(P64, 3)
   CX(P32, 0) CX(P32, 1) CX(P32, 2) CX(P32, 3)
   CX(PDF, 0) CX(PDF, 1) CX(PDF, 2) CX(PDF, 3)
 #undef CX
-#undef CXK
   return cudaErrorInvalidValue;
 }
 

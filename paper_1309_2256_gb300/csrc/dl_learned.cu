@@ -23,6 +23,11 @@ struct dl_nn {
   int adam_t = 0;  // Adam steps taken
   double* dscal = nullptr;  // device scalars: [0, 2) dot products, [2, 2 + 2 * nloss) loss partial sums
   int nloss = 0;
+  // tensor-core forward (bfloat16 activations): per layer 36 B chunks of 2 KB laid out from W
+  bool use_tc = false;
+  bool tc_dirty = true;     // W changed since the chunks were laid out
+  void* tcB = nullptr;
+  int* tc_err = nullptr;    // set by the kernel when a bounded wait ran out
 };
 
 using namespace dlh;
@@ -59,14 +64,40 @@ dl_status get_acts(dl_nn* nn, const char* tag, int l0, Acts& A) {
   return DL_OK;
 }
 
-// X[l+1] = layer_l(X[l]) for every layer, both output parities.
+constexpr size_t TC_LAYER_BYTES = 36 * 2048;
+
+// X[l+1] = layer_l(X[l]) for every layer, both output parities: on the tensor cores
+// for bfloat16 activations (when enabled), else on the CUDA cores.
 dl_status forward(dl_nn* nn, const Acts& X) {
   dl_ctx* c = nn->c;
   const LatDesc L = make_batch(c, 1).lat[0];
+  if (nn->use_tc && nn->tc_dirty) {
+    for (int l = 0; l < nn->nl; ++l)
+      CK(dl::nn_tc_prep(nn->W + nn->woff[l], nn->ci[l], nn->co[l], (char*)nn->tcB + l * TC_LAYER_BYTES, c->st));
+    nn->tc_dirty = false;
+  }
   for (int l = 0; l < nn->nl; ++l)
-    for (int p = 0; p < 2; ++p)
-      CK(dl::nn_forward(L, nn->act, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(), p ? X.o[l + 1]->ref() : X.e[l + 1]->ref(),
-                        c->g32, nn->W + nn->woff[l], nn->ci[l], nn->co[l], lg_in(nn, l), lg_out(nn, l), c->st));
+    for (int p = 0; p < 2; ++p) {
+      FieldRef out = p ? X.o[l + 1]->ref() : X.e[l + 1]->ref();
+      if (nn->use_tc)
+        CK(dl::nn_forward_tc(L, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(), out, c->g32,
+                             (const char*)nn->tcB + l * TC_LAYER_BYTES, nn->ci[l], nn->co[l], lg_in(nn, l),
+                             lg_out(nn, l), nn->tc_err, c->st));
+      else
+        CK(dl::nn_forward(L, nn->act, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(), out, c->g32, nn->W + nn->woff[l],
+                          nn->ci[l], nn->co[l], lg_in(nn, l), lg_out(nn, l), c->st));
+    }
+  return DL_OK;
+}
+
+// the tensor-core kernels' bounded waits: an expired wait is an error of the call
+dl_status check_tc(dl_nn* nn) {
+  dl_ctx* c = nn->c;
+  if (!nn->use_tc) return DL_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, nn->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (h) return fail(c, DL_ERR_CUDA, "tensor-core forward: a bounded wait expired");
   return DL_OK;
 }
 
@@ -256,6 +287,10 @@ dl_status dl_nn_create(dl_ctx* c, int n_layers, int channels, int act_prec, dl_n
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->v, sizeof(float2) * nn->nw);
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->wpart, sizeof(float2) * nn->npart * nn->slots);
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->dscal, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nn->tcB, TC_LAYER_BYTES * n_layers);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&nn->tc_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(nn->tc_err, 0, sizeof(int));
+  nn->use_tc = nn->act == PBF;  // bfloat16 activations run on the tensor cores by default
   if (e == cudaSuccess) {
     nn->nloss = 2;
     e = cudaMemset(nn->W, 0, sizeof(float2) * nn->nw);
@@ -282,10 +317,20 @@ void dl_nn_destroy(dl_nn* nn) {
   cudaFree(nn->v);
   cudaFree(nn->wpart);
   cudaFree(nn->dscal);
+  cudaFree(nn->tcB);
+  cudaFree(nn->tc_err);
   delete nn;
 }
 
 long long dl_nn_weight_count(const dl_nn* nn) { return nn ? (long long)nn->nw : 0; }
+
+dl_status dl_nn_set_tensor_cores(dl_nn* nn, int enable) {
+  if (!valid_nn(nn)) return DL_ERR_ARG;
+  if (enable && nn->act != PBF) return fail(nn->c, DL_ERR_ARG, "the tensor-core forward needs bfloat16 activations");
+  nn->use_tc = enable != 0;
+  nn->tc_dirty = true;
+  return DL_OK;
+}
 
 dl_status dl_nn_set_weights(dl_nn* nn, const float* w) {
   if (!valid_nn(nn) || !w) return DL_ERR_ARG;
@@ -293,6 +338,7 @@ dl_status dl_nn_set_weights(dl_nn* nn, const float* w) {
   dl_status s;
   if ((s = enter(c)) != DL_OK) return s;
   CK(cudaMemcpyAsync(nn->W, w, sizeof(float2) * nn->nw, cudaMemcpyHostToDevice, c->st));
+  nn->tc_dirty = true;
   CK(cudaMemsetAsync(nn->m, 0, sizeof(float2) * nn->nw, c->st));
   CK(cudaMemsetAsync(nn->v, 0, sizeof(float2) * nn->nw, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -326,6 +372,7 @@ dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype) {
     for (int p = 0; p < 2; ++p)
       CK(dl::unpack(B1, nn->act, p, (char*)out + off, p ? X.o[nn->nl]->ref() : X.e[nn->nl]->ref(), dtype, c->st));
   }
+  if ((s = check_tc(nn)) != DL_OK) return s;
   return leave(c);
 }
 
@@ -371,6 +418,7 @@ dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int 
   if (grad) CK(cudaMemcpyAsync(grad, nn->grad, sizeof(float2) * nn->nw, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   if (loss) *loss = L;
+  if ((st = check_tc(nn)) != DL_OK) return st;
   return leave(c);
 }
 
@@ -423,9 +471,11 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, con
     nn->adam_t += 1;
     CK(dl::nn_adam(nn->W, nn->grad, nn->m, nn->v, nn->nw, (float)prm->lr, (float)prm->beta1, (float)prm->beta2,
                    (float)prm->eps, nn->adam_t, 1.f / (float)prm->batch, c->st));
+    nn->tc_dirty = true;
     if (loss_hist) loss_hist[step] = L / prm->batch;
   }
   CK(cudaStreamSynchronize(c->st));
+  if ((st = check_tc(nn)) != DL_OK) return st;
   return leave(c);
 }
 
@@ -603,6 +653,7 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
     st.true_resid[k] = bn > 0.0 ? rn / bn : 0.0;
   }
   CK(cudaStreamSynchronize(c->st));
+  if (nn && (s = check_tc(nn)) != DL_OK) return s;
   st.op_applications = nop;
   st.nn_applications = nnn;
   st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -448,6 +448,248 @@ __global__ void copy_col_kernel(LatDesc L, FieldRef dst, int lgd, int cd, FieldR
   SIO<PD>::store(seg_ptr_w<PD>(dst, L), seg_norm(dst, L), nd, (i << lgd) + cd, w);
 }
 
+
+// ------------------------------------------------ forward on the tensor cores
+// bfloat16 activations: the channel mixing of a layer is a dense contraction,
+// for each spin half h and spin-colour component c6 of that half
+//   Y_(h,c6)[site][o] = sum_(t, i, kind) F_(t,i,kind)(site, h, c6) C_(h,t,kind)[o][i],
+// F the transported inputs (kind 0: U x_i, kind 1: g_mu U x_i) and C the weight
+// combinations of the spin factors on that half (W0 +- W2, W1 +- W3; +- = g5).
+// As real GEMMs: M = 128 sites of one parity per CTA, N = 32 (16 channels x re/im),
+// K = 64 per (term, kind) chunk (16 channels x re/im x re/im of F folded into B).
+// Each chunk: 128 threads transport and write 12 bf16 A tiles (one per (h, c6)) in
+// the no-swizzle K-major core-matrix layout; one thread issues 24 tcgen05.mma
+// (M128 N32 K16, FP32 accumulators in TMEM: 12 x 32 columns), commits to an
+// mbarrier, and the CTA waits (bounded) before the next chunk overwrites the tiles.
+// B (the weights) is laid out once per layer by nn_tc_prep_kernel.
+constexpr int TC_M = 128;
+constexpr int TC_ATILE = TC_M * 32 * 2;  // bytes of one A tile (128 rows x 32 bf16)
+constexpr int TC_BCHUNK = 32 * 32 * 2;   // bytes of one B chunk (32 rows x 32 bf16)
+constexpr int TC_SMEM = 12 * TC_ATILE + 2 * TC_BCHUNK + 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; LBO = 128 B between the two
+// 8 x 16 B core matrices adjacent in K, SBO = 512 B between 8-row groups
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+// byte offset of element (row r, k) of a 32-wide K tile
+__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+// B chunks of one layer: [h 2][t 9][kind 2] x (32 n x 32 k), n = 2 o + part_y, k = 2 i + part_F
+__global__ void nn_tc_prep_kernel(const float2* __restrict__ W, int CI, int CO, __nv_bfloat16* __restrict__ Bc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 36 * 1024) return;
+  const int chunk = e >> 10, w = e & 1023;
+  const int n = w >> 5, k = w & 31;
+  const int h = chunk / 18, t = (chunk / 2) % 9, kind = chunk & 1;
+  const int o = n >> 1, py = n & 1, i = k >> 1, pf = k & 1;
+  float cr = 0.f, ci = 0.f;
+  if (o < CO && i < CI && !(t == 0 && kind == 1)) {
+    const size_t tb = (size_t)CO * CI;
+    const float sg = h ? -1.f : 1.f;
+    float2 a, b;
+    if (t == 0) {
+      a = W[(size_t)o * CI + i];
+      b = W[tb + (size_t)o * CI + i];
+    } else {
+      a = W[(4 * t + kind) * tb + (size_t)o * CI + i];
+      b = W[(4 * t + kind + 2) * tb + (size_t)o * CI + i];
+    }
+    cr = a.x + sg * b.x;
+    ci = a.y + sg * b.y;
+  }
+  // y_re += c_re F_re - c_im F_im ; y_im += c_im F_re + c_re F_im
+  const float v = py == 0 ? (pf == 0 ? cr : -ci) : (pf == 0 ? ci : cr);
+  Bc[(size_t)chunk * 1024 + tc_off(n, k) / 2] = __float2bfloat16_rn(v);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, FieldRef xe, FieldRef xo, FieldRef y,
+                                                           const void* __restrict__ g32,
+                                                           const __nv_bfloat16* __restrict__ Bc, int CI, int CO,
+                                                           int lgin, int lgout, int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sA = tc_smem;                          // 12 A tiles
+  unsigned char* sB = tc_smem + 12 * TC_ATILE;          // 2 B chunks (halves)
+  uint64_t* mbar = (uint64_t*)(sB + 2 * TC_BCHUNK);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int site = blockIdx.x * TC_M + tid;
+  const bool live = site < L.Vh;
+  const long long nin = (long long)L.Vh << lgin, nout = (long long)L.Vh << lgout;
+  const FieldRef& xs = p ? xo : xe;
+  const FieldRef& xn = p ? xe : xo;
+  const void* gb = gauge_seg<G>(g32, L);
+  int x = 0, yy = 0, z = 0, t = 0;
+  if (live) cb_coords(L, site, p, x, yy, z, t);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  // M = 128, N = 32, A and B bf16 K-major, D FP32
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  bool ok = true;
+  int chunk = 0;
+  for (int term = 0; term < 9 && ok; ++term) {
+    // this term's link and neighbour (terms 1 + 2 mu forward, 2 + 2 mu backward)
+    float u[18];
+    long long nbr = site;
+    if (term > 0 && live) {
+      const int d = term - 1, mu = d >> 1;
+      const bool bwd = d & 1;
+      int xn_ = x, yn = yy, zn = z, tn = t;
+      bool crosses = false;
+      if (mu == 0) xn_ = bwd ? (x == 0 ? L.X - 1 : x - 1) : (x + 1 == L.X ? 0 : x + 1);
+      else if (mu == 1) yn = bwd ? (yy == 0 ? L.Y - 1 : yy - 1) : (yy + 1 == L.Y ? 0 : yy + 1);
+      else if (mu == 2) zn = bwd ? (z == 0 ? L.Z - 1 : z - 1) : (z + 1 == L.Z ? 0 : z + 1);
+      else {
+        crosses = bwd ? (t == 0) : (t + 1 == L.T);
+        tn = bwd ? (t == 0 ? L.T - 1 : t - 1) : (t + 1 == L.T ? 0 : t + 1);
+      }
+      nbr = lex_of(L, xn_, yn, zn, tn) >> 1;
+      GIO<G>::load(gb, L.Vh, bwd ? 1 - p : p, mu, bwd ? (int)nbr : site, u);
+      const float f = crosses ? (float)L.tbc : 1.f;
+#pragma unroll
+      for (int e = 0; e < 18; ++e) u[e] *= f;
+    }
+    for (int kind = 0; kind < (term == 0 ? 1 : 2) && ok; ++kind, ++chunk) {
+      if (chunk > 0) {  // the previous chunk's MMAs must have read the tiles
+        int done = 0;
+        for (int it = 0; it < (1 << 24) && !done; ++it) {
+          uint32_t r;
+          asm volatile(
+              "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+              : "=r"(r)
+              : "r"(smem_u32(mbar)), "r"((uint32_t)((chunk - 1) & 1)));
+          done = r;
+        }
+        if (!done) {
+          ok = false;
+          if (tid == 0) atomicExch(err, 1);
+          break;
+        }
+      }
+      // A tiles: this thread's row, 16 channels
+      for (int i = 0; i < 16; ++i) {
+        float v[24];
+        if (live && i < CI) {
+          if (term == 0) {
+            SIO<PBF>::load(seg_ptr<PBF>(xs, L), nullptr, nin, ((long long)site << lgin) + i, v);
+          } else {
+            float w0[24];
+            const int d = term - 1;
+            SIO<PBF>::load(seg_ptr<PBF>(xn, L), nullptr, nin, (nbr << lgin) + i, w0);
+            colour_mul(u, w0, v, (d & 1) != 0);
+            if (kind == 1) {
+              float g[24];
+              gamma_apply_rt(d >> 1, v, g);
+#pragma unroll
+              for (int m = 0; m < 24; ++m) v[m] = g[m];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 24; ++m) v[m] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < 12; ++m)
+          *(__nv_bfloat162*)(sA + m * TC_ATILE + tc_off(tid, 2 * i)) = __floats2bfloat162_rn(v[2 * m], v[2 * m + 1]);
+      }
+      // B chunks of both halves for (term, kind)
+      for (int e = tid; e < 2 * TC_BCHUNK / 16; e += blockDim.x) {
+        const int h = e / (TC_BCHUNK / 16), q = e % (TC_BCHUNK / 16);
+        const uint4* src = (const uint4*)(Bc + (size_t)((h * 9 + term) * 2 + kind) * 1024);
+        ((uint4*)(sB + h * TC_BCHUNK))[q] = __ldg(src + q);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+#pragma unroll 1
+        for (int g = 0; g < 12; ++g)
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t da = tc_desc(smem_u32(sA + g * TC_ATILE + ks * 256));
+            const uint64_t db = tc_desc(smem_u32(sB + (g / 6) * TC_BCHUNK + ks * 256));
+            const uint32_t acc = (chunk > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(tmem + (uint32_t)(g * 32)),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
+      }
+    }
+  }
+  // wait for the last chunk's MMAs (also on an error path: nothing may be in flight at dealloc)
+  {
+    int done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+      uint32_t r;
+      asm volatile(
+          "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+          : "=r"(r)
+          : "r"(smem_u32(mbar)), "r"((uint32_t)((chunk - 1) & 1)));
+      done = r;
+    }
+    if (!done) {
+      ok = false;
+      if (tid == 0) atomicExch(err, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // epilogue: this thread's site = TMEM lane; chunk kk of the bf16 output holds components 4 kk .. 4 kk + 3
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int kk = 0; kk < 3; ++kk) {
+      uint32_t r[4][32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t ta = lane_base + (uint32_t)((4 * kk + q) * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]),
+              "=r"(r[q][7]), "=r"(r[q][8]), "=r"(r[q][9]), "=r"(r[q][10]), "=r"(r[q][11]), "=r"(r[q][12]),
+              "=r"(r[q][13]), "=r"(r[q][14]), "=r"(r[q][15]), "=r"(r[q][16]), "=r"(r[q][17]), "=r"(r[q][18]),
+              "=r"(r[q][19]), "=r"(r[q][20]), "=r"(r[q][21]), "=r"(r[q][22]), "=r"(r[q][23]), "=r"(r[q][24]),
+              "=r"(r[q][25]), "=r"(r[q][26]), "=r"(r[q][27]), "=r"(r[q][28]), "=r"(r[q][29]), "=r"(r[q][30]),
+              "=r"(r[q][31])
+            : "r"(ta));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (live) {
+        uint4* out = (uint4*)seg_ptr_w<PBF>(y, L);
+#pragma unroll
+        for (int o = 0; o < 16; ++o)
+          if (o < CO) {
+            uint4 c;
+            __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              hh[q] = __floats2bfloat162_rn(__uint_as_float(r[q][2 * o]), __uint_as_float(r[q][2 * o + 1]));
+            out[kk * nout + ((long long)site << lgout) + o] = c;
+          }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 }  // namespace
 
 namespace dl {
@@ -535,6 +777,33 @@ cudaError_t copy_col(const LatDesc& L, int pd, int ps, FieldRef dst, int lgd, in
   CC(P32, P32) CC(P32, PBF) CC(PBF, P32) CC(P64, PBF) CC(PBF, P64) CC(P64, P32) CC(P32, P64) CC(P64, P64)
 #undef CC
   return cudaErrorInvalidValue;
+}
+
+cudaError_t nn_tc_prep(const float2* W, int ci, int co, void* Bc, cudaStream_t st) {
+  if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
+  DL_COUNT();
+  nn_tc_prep_kernel<<<36 * 1024 / 256, 256, 0, st>>>(W, ci, co, (__nv_bfloat16*)Bc);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_forward_tc(const LatDesc& L, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef y, const void* g32,
+                          const void* Bc, int ci, int co, int lgin, int lgout, int* err, cudaStream_t st) {
+  if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
+  const int grid = (L.Vh + TC_M - 1) / TC_M;
+  if (grec == 12) {
+    cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R12>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    DL_COUNT();
+    nn_fwd_tc_kernel<G32R12><<<grid, 128, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
+                                                          lgin, lgout, err);
+  } else if (grec == 8) {
+    cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    DL_COUNT();
+    nn_fwd_tc_kernel<G32R8><<<grid, 128, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
+                                                         lgin, lgout, err);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace dl

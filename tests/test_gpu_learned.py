@@ -85,6 +85,38 @@ def test_forward_matches_oracle(dl, act, tol, n_layers, c):
         assert np.abs(got[r] - ref).max() <= tol * np.abs(ref).max(), r
 
 
+def test_tensor_core_forward_matches_cuda_core_forward(dl):
+    """bfloat16 network, 16 channels on an 8^4 lattice (several 128-site CTAs): the
+    tcgen05 channel mixing against the CUDA-core forward and against the oracle."""
+    dims = (8, 8, 8, 8)
+    links = synth.gauge_links(dims, 0.4, 317)
+    w = synth.network_weights(4, 16, 65, scale=0.6, identity=0.5)
+    eta = np.stack([noise.z4_noise(dims, 15, r) for r in range(2)])
+    ctx = _ctx(dl, dims, links, 0.16, 0.01)
+    outs = {}
+    try:
+        nn = dl.dl_nn_create(ctx, 4, 16, dl.DL_BF16)
+        dl.dl_nn_set_weights(nn, w)
+        for tc in (1, 0):
+            dl.dl_nn_set_tensor_cores(nn, tc)
+            out = torch.zeros(eta.size, dtype=torch.complex128, device="cuda")
+            dl.dl_nn_apply(nn, 2, _dev(eta), out)
+            outs[tc] = out.cpu().numpy().reshape(eta.shape)
+        dl.dl_nn_destroy(nn)
+        nn32 = dl.dl_nn_create(ctx, 4, 16, dl.DL_F32)
+        with pytest.raises(dl.DLError):
+            dl.dl_nn_set_tensor_cores(nn32, 1)
+        dl.dl_nn_destroy(nn32)
+    finally:
+        dl.dl_destroy(ctx)
+    ws = _to_oracle(w, 4, 16)
+    for r in range(2):
+        ref, _ = network.forward(links, ws, eta[r])
+        sc = np.abs(ref).max()
+        assert np.abs(outs[1][r] - ref).max() <= 3e-2 * sc, r
+        assert np.abs(outs[1][r] - outs[0][r]).max() <= 3e-2 * sc, r
+
+
 def test_adjoint_matches_oracle(dl):
     """N^+ y from the input-gradient kernels against the oracle's layer adjoints (FP32)."""
     dims = (4, 4, 4, 4)
