@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances: FP64 operators <= 1e-13 relative, FP32 <= 2e-6 (the bounds of the
-benchmark spec), 16-bit storage <= 3e-4 (int16 fixed point with a
+Tolerances: FP64 operators <= 1e-13 relative, FP32 <= 2e-6 (the target bounds of
+this path), 16-bit storage <= 3e-4 (int16 fixed point with a
 per-site scale); noise and indexing bit-exact; loops from solves converged to CG residual
 1e-10 within 1e-8 of the dense-inverse loops.
 """
