@@ -457,7 +457,7 @@ __global__ void copy_col_kernel(LatDesc L, FieldRef dst, int lgd, int cd, FieldR
 // combinations of the spin factors on that half (W0 +- W2, W1 +- W3; +- = g5).
 // As real GEMMs: M = 128 sites of one parity per CTA, N = 32 (16 channels x re/im),
 // K = 64 per (term, kind) chunk (16 channels x re/im x re/im of F folded into B).
-// Each chunk: 128 threads transport and write 12 bf16 A tiles (one per (h, c6)) in
+// Each chunk: 256 threads (two per site) transport and write 12 bf16 A tiles (one per (h, c6)) in
 // the no-swizzle K-major core-matrix layout; one thread issues 24 tcgen05.mma
 // (M128 N32 K16, FP32 accumulators in TMEM: 12 x 32 columns), commits to an
 // mbarrier, and the CTA waits (bounded) before the next chunk overwrites the tiles.
@@ -509,8 +509,11 @@ __global__ void nn_tc_prep_kernel(const float2* __restrict__ W, int CI, int CO, 
   Bc[(size_t)chunk * 1024 + tc_off(n, k) / 2] = __float2bfloat16_rn(v);
 }
 
+// 256 threads: thread tid transports channels 8 (tid >> 7) .. 8 (tid >> 7) + 7 of site
+// tid & 127; in the epilogue warps w and w + 4 share TMEM lanes 32 (w & 3) .. and
+// write output channels 0..7 and 8..15 of those sites.
 template <int G>
-__global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, FieldRef xe, FieldRef xo, FieldRef y,
+__global__ void __launch_bounds__(256, 1) nn_fwd_tc_kernel(LatDesc L, int p, FieldRef xe, FieldRef xo, FieldRef y,
                                                            const void* __restrict__ g32,
                                                            const __nv_bfloat16* __restrict__ Bc, int CI, int CO,
                                                            int lgin, int lgout, int* err) {
@@ -520,7 +523,8 @@ __global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
   uint64_t* mbar = (uint64_t*)(sB + 2 * TC_BCHUNK);
   uint32_t* tslot = (uint32_t*)(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int site = blockIdx.x * TC_M + tid;
+  const int row = tid & (TC_M - 1), half = tid >> 7;
+  const int site = blockIdx.x * TC_M + row;
   const bool live = site < L.Vh;
   const long long nin = (long long)L.Vh << lgin, nout = (long long)L.Vh << lgout;
   const FieldRef& xs = p ? xo : xe;
@@ -582,8 +586,8 @@ __global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
           break;
         }
       }
-      // A tiles: this thread's row, 16 channels
-      for (int i = 0; i < 16; ++i) {
+      // A tiles: this thread's row, its 8 channels
+      for (int i = 8 * half; i < 8 * half + 8; ++i) {
         float v[24];
         if (live && i < CI) {
           if (term == 0) {
@@ -606,7 +610,7 @@ __global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
         }
 #pragma unroll
         for (int m = 0; m < 12; ++m)
-          *(__nv_bfloat162*)(sA + m * TC_ATILE + tc_off(tid, 2 * i)) = __floats2bfloat162_rn(v[2 * m], v[2 * m + 1]);
+          *(__nv_bfloat162*)(sA + m * TC_ATILE + tc_off(row, 2 * i)) = __floats2bfloat162_rn(v[2 * m], v[2 * m + 1]);
       }
       // B chunks of both halves for (term, kind)
       for (int e = tid; e < 2 * TC_BCHUNK / 16; e += blockDim.x) {
@@ -652,36 +656,36 @@ __global__ void __launch_bounds__(128, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // epilogue: this thread's site = TMEM lane; chunk kk of the bf16 output holds components 4 kk .. 4 kk + 3
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    // epilogue: this thread's site = TMEM lane; chunk kk of the bf16 output holds components
+    // 4 kk .. 4 kk + 3; this warp reads the 16 columns (8 channels x re/im) of its half
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(16 * half);
     for (int kk = 0; kk < 3; ++kk) {
-      uint32_t r[4][32];
+      uint32_t r[4][16];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint32_t ta = lane_base + (uint32_t)((4 * kk + q) * 32);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(r[q][0]), "=r"(r[q][1]), "=r"(r[q][2]), "=r"(r[q][3]), "=r"(r[q][4]), "=r"(r[q][5]), "=r"(r[q][6]),
               "=r"(r[q][7]), "=r"(r[q][8]), "=r"(r[q][9]), "=r"(r[q][10]), "=r"(r[q][11]), "=r"(r[q][12]),
-              "=r"(r[q][13]), "=r"(r[q][14]), "=r"(r[q][15]), "=r"(r[q][16]), "=r"(r[q][17]), "=r"(r[q][18]),
-              "=r"(r[q][19]), "=r"(r[q][20]), "=r"(r[q][21]), "=r"(r[q][22]), "=r"(r[q][23]), "=r"(r[q][24]),
-              "=r"(r[q][25]), "=r"(r[q][26]), "=r"(r[q][27]), "=r"(r[q][28]), "=r"(r[q][29]), "=r"(r[q][30]),
-              "=r"(r[q][31])
+              "=r"(r[q][13]), "=r"(r[q][14]), "=r"(r[q][15])
             : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (live) {
         uint4* out = (uint4*)seg_ptr_w<PBF>(y, L);
 #pragma unroll
-        for (int o = 0; o < 16; ++o)
+        for (int oo = 0; oo < 8; ++oo) {
+          const int o = 8 * half + oo;
           if (o < CO) {
             uint4 c;
             __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&c);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              hh[q] = __floats2bfloat162_rn(__uint_as_float(r[q][2 * o]), __uint_as_float(r[q][2 * o + 1]));
+              hh[q] = __floats2bfloat162_rn(__uint_as_float(r[q][2 * oo]), __uint_as_float(r[q][2 * oo + 1]));
             out[kk * nout + ((long long)site << lgout) + o] = c;
           }
+        }
       }
     }
   }
@@ -793,12 +797,12 @@ cudaError_t nn_forward_tc(const LatDesc& L, int grec, int parity, FieldRef xe, F
   if (grec == 12) {
     cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R12>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     DL_COUNT();
-    nn_fwd_tc_kernel<G32R12><<<grid, 128, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
+    nn_fwd_tc_kernel<G32R12><<<grid, 256, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
                                                           lgin, lgout, err);
   } else if (grec == 8) {
     cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     DL_COUNT();
-    nn_fwd_tc_kernel<G32R8><<<grid, 128, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
+    nn_fwd_tc_kernel<G32R8><<<grid, 256, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
                                                          lgin, lgout, err);
   } else {
     return cudaErrorInvalidValue;
