@@ -87,3 +87,21 @@ def test_loss_vanishes_at_exact_map():
     loss, grads = network.loss_and_grads(links, weights, [(eta, out)])
     assert loss < 1e-28
     assert all(np.abs(v).max() < 1e-12 for gw in grads for v in gw.values())
+
+
+def test_layer_adjoint_is_the_adjoint():
+    """<y, L x> = <L^+ y, x> for the input gradient of every layer shape (1->C, C->C, C->1),
+    and the chain over layers is the adjoint of the network."""
+    rng = np.random.default_rng(7)
+    links = synth.gauge_links(DIMS, 0.4, 85)
+    weights = _small_net(rng, c=3)
+    x = synth.gaussian_spinors(DIMS, 1, 91)
+    y = synth.gaussian_spinors(DIMS, 1, 92)
+    nx, _ = network.forward(links, weights, x[0])
+    g = y
+    for li in range(len(weights) - 1, -1, -1):
+        cin = weights[li]["W0"].shape[1]
+        _, g = network.layer_backward(links, weights[li], np.zeros((cin,) + x.shape[1:], dtype=np.complex128), g)
+    lhs = np.vdot(y[0], nx)
+    rhs = np.vdot(g[0], x[0])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
