@@ -249,7 +249,7 @@ dl_status nn_map_block(dl_nn* nn, dl_ctx* c, const Batch& B, Field* ee, Field* e
     CK(dl::copy_col(L, P32, nn->act, xe->ref(), lg, j, X.e[nn->nl]->ref(), 0, 0, c->st));
     CK(dl::copy_col(L, P32, nn->act, xo->ref(), lg, j, X.o[nn->nl]->ref(), 0, 0, c->st));
   }
-  return DL_OK;
+  return check_tc(nn);
 }
 }  // namespace dlh
 
