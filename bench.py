@@ -176,7 +176,7 @@ def run_ours(args, rank, world, device):
         return dl.dl_tsm_params(n_hp=n_hp_s, n_lp=n_lp_s, tol_hp=TOL_HP, tol_lp=TOL_LP, prec_hp_lo=dl.DL_F32,
                                 prec_lp_lo=dl.DL_F16, delta_hp=args.delta_hp, block=BLOCK,
                                 seed=rank_seed(step, rank), p2max=P2MAX, with_deriv=0,
-                                hpe=1, max_iter=200000, chunk=32, hp_guess=1)
+                                hpe=1, max_iter=200000, chunk=32, hp_guess=1, hpe_diff=1)
 
     loops = np.zeros((3, DIMS[3], npm, 1, 4, 4), dtype=np.complex128)
     obs = {"hp": [], "pair": [], "lp": []}
@@ -629,7 +629,7 @@ def main():
         "dtype": "f16/f32 Krylov, f64 reliable updates and accumulation",
         "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
-                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "hp_from_lp": 1, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
+                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "hp_from_lp": 1, "hpe_correction_from_difference": 1, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
                    "step": "one TSM sweep: 24 HP-LP pairs + 500 LP solves + contractions",
                    "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

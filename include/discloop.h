@@ -201,6 +201,11 @@ typedef struct {
   int hp_guess;          /* 1: every HP solve starts from the LP solution of its noise
                             vector (the HP tolerance is unchanged, so the HP solution is
                             the same to that tolerance); 0: from zero */
+  int hpe_diff;          /* 1: the HPE estimator's HP-LP correction (Eq. estiTSM) is
+                            computed from s_HP - s_LP, which the estimator is linear in:
+                            eta^+ X (BH)^4 (s_HP - s_LP) with (BH)^4 applied in FP32 to the
+                            difference taken in high precision (relative error ~1e-7 of the
+                            correction, not of the loop); 0: both terms in high precision */
 } dl_tsm_params;
 
 typedef struct {

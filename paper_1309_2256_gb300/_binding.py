@@ -42,7 +42,7 @@ class dl_tsm_params(C.Structure):
     _fields_ = [("n_hp", C.c_int), ("n_lp", C.c_int), ("tol_hp", C.c_double), ("tol_lp", C.c_double),
                 ("prec_hp_lo", C.c_int), ("prec_lp_lo", C.c_int), ("delta_hp", C.c_double), ("block", C.c_int),
                 ("seed", C.c_uint64), ("p2max", C.c_int), ("with_deriv", C.c_int), ("hpe", C.c_int),
-                ("max_iter", C.c_int), ("chunk", C.c_int), ("lp_net", C.c_void_p), ("hp_guess", C.c_int)]
+                ("max_iter", C.c_int), ("chunk", C.c_int), ("lp_net", C.c_void_p), ("hp_guess", C.c_int), ("hpe_diff", C.c_int)]
 
 
 class dl_tsm_info(C.Structure):

@@ -1348,7 +1348,22 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     (hp ? t_hp : t_lp) += std::chrono::duration<double>(t1 - t0).count();
     for (int e = 0; e < n_est; ++e) {
       double2* o = out + (size_t)e * per * blk;
-      if (est_mode[e] == DL_EST_HPE) {
+      if (est_mode[e] == DL_EST_HPE && hp && prm->hpe_diff) {
+        // the HPE estimator is linear in s: its HP-LP correction is eta^+ X (BH)^4 (s_HP - s_LP),
+        // with the difference taken in double-float and (BH)^4 applied to it in FP32
+        Field *lxe, *lxo, *de, *dd, *e3, *o3, *we, *wo;
+        if ((s2 = ensure_field(c, "ts_xe32", P32, B, &lxe)) || (s2 = ensure_field(c, "ts_po32", P32, B, &lxo)) ||
+            (s2 = ensure_field(c, "ts_hde", P32, B, &de)) || (s2 = ensure_field(c, "ts_hdo", P32, B, &dd)) ||
+            (s2 = ensure_field(c, "ts_hee", P32, B, &e3)) || (s2 = ensure_field(c, "ts_heo", P32, B, &o3)))
+          return s2;
+        CK(dl::diff(B, P32, hi, P32, de->ref(), xe->ref(), lxe->ref(), c->st));
+        CK(dl::diff(B, P32, hi, P32, dd->ref(), po->ref(), lxo->ref(), c->st));
+        CK(dl::copy(B, P32, hi, e3->ref(), ee->ref(), nullptr, c->st));
+        CK(dl::copy(B, P32, hi, o3->ref(), eo->ref(), nullptr, c->st));
+        if ((s2 = bh_power(c, B, P32, 1, 4, de, dd, &we, &wo)) != DL_OK) return s2;
+        if ((s2 = contract_internal(c, B, P32, DL_EST_HPE, 0, prm->p2max, we, wo, e3, o3, 1.0, 0.0, o, 0)) != DL_OK)
+          return s2;
+      } else if (est_mode[e] == DL_EST_HPE) {
         Field *we, *wo;
         if ((s2 = bh_power(c, B, hi, 1, 4, xe, po, &we, &wo)) != DL_OK) return s2;
         if ((s2 = contract_internal(c, B, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0)) != DL_OK) return s2;
@@ -1382,9 +1397,12 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     memset(&st, 0, sizeof(st));
     if ((s = run_block(n, (uint64_t)b0, true, bh, obs2, &st)) < 0) return s;
     for (int i = 0; i < n; ++i) inf.iters_hp += st.iters[i];
-    for (int e = 0; e < n_est; ++e)
-      CK(dl::col_accumulate(bh + (size_t)e * per * blk, bl + (size_t)e * per * blk, n, per, 1.0, acc_d + (size_t)e * per,
-                            c->st));
+    for (int e = 0; e < n_est; ++e) {
+      // with hpe_diff the HP block already holds the HPE correction itself
+      const bool direct = est_mode[e] == DL_EST_HPE && prm->hpe_diff;
+      CK(dl::col_accumulate(bh + (size_t)e * per * blk, direct ? nullptr : bl + (size_t)e * per * blk, n, per, 1.0,
+                            acc_d + (size_t)e * per, c->st));
+    }
     if (obs_lp_pair) {
       CK(cudaMemcpyAsync(hbuf.data(), obs1, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));

@@ -32,6 +32,23 @@ __global__ void copy_kernel(Batch B, FieldRef dst, FieldRef src, const int* mask
   SIO<PD>::store(seg_ptr_w<PD>(dst, L), seg_norm(dst, L), nitems, j, w);
 }
 
+// out = a - b, the difference evaluated in a's arithmetic, stored in out's precision
+template <int PO, int PA, int PB>
+__global__ void diff_kernel(Batch B, FieldRef out, FieldRef a, FieldRef b) {
+  const int* mask = nullptr;
+  ITEM_PROLOGUE
+  if (!act) return;
+  typedef typename SIO<PA>::real RA;
+  RA av[24];
+  typename SIO<PB>::real bv[24];
+  typename SIO<PO>::real ov[24];
+  SIO<PA>::load(seg_ptr<PA>(a, L), seg_norm(a, L), nitems, j, av);
+  SIO<PB>::load(seg_ptr<PB>(b, L), seg_norm(b, L), nitems, j, bv);
+#pragma unroll
+  for (int m = 0; m < 24; ++m) ov[m] = (typename SIO<PO>::real)(av[m] - (RA)bv[m]);
+  SIO<PO>::store(seg_ptr_w<PO>(out, L), seg_norm(out, L), nitems, j, ov);
+}
+
 // x += y, then y = 0
 template <int PH, int PL>
 __global__ void accum_kernel(Batch B, FieldRef x, FieldRef y, const int* mask, int zero_y) {
@@ -429,6 +446,23 @@ cudaError_t sum_partials(const Batch& Bin, const double* partial, double* out, i
   DL_COUNT();
   sum_partials_kernel<<<ncols_total, 1024, 0, st>>>(B, partial, out, stride, slot);
   return cudaGetLastError();
+}
+
+cudaError_t diff(const Batch& Bin, int po, int pa, int pb, FieldRef out, FieldRef a, FieldRef b, cudaStream_t st) {
+  Batch B = Bin;
+  const int g = grid_of(B);
+  if (!g) return cudaSuccess;
+  if (po == P32 && pa == PDF && pb == P32) {
+    DL_COUNT();
+    diff_kernel<P32, PDF, P32><<<g, 256, 0, st>>>(B, out, a, b);
+    return cudaGetLastError();
+  }
+  if (po == P32 && pa == P64 && pb == P32) {
+    DL_COUNT();
+    diff_kernel<P32, P64, P32><<<g, 256, 0, st>>>(B, out, a, b);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t cg_alpha(int ncols, double* S, int* active, int* flags, cudaStream_t st) {

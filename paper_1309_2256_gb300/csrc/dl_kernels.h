@@ -25,6 +25,8 @@ cudaError_t copy(const Batch& B, int pd, int ps, FieldRef dst, FieldRef src, con
 cudaError_t accum(const Batch& B, int ph, int pl, FieldRef x, FieldRef y, const int* mask, int zero_y, cudaStream_t st);
 cudaError_t xmy_norm(const Batch& B, int prec, FieldRef r, FieldRef b, FieldRef a, const int* mask, double* partial,
                      cudaStream_t st);
+// out (po) = a (pa) - b (pb), evaluated in a's arithmetic (FP32 out from a high-precision a and an FP32 b)
+cudaError_t diff(const Batch& B, int po, int pa, int pb, FieldRef out, FieldRef a, FieldRef b, cudaStream_t st);
 cudaError_t norm2(const Batch& B, int prec, FieldRef v, const int* mask, double* partial, cudaStream_t st);
 cudaError_t xpay(const Batch& B, int prec, FieldRef p, FieldRef r, const double* beta, const int* mask, cudaStream_t st);
 cudaError_t twist(const Batch& B, int prec, FieldRef out, FieldRef in, const EpiSet& ep, const int* mask, cudaStream_t st);

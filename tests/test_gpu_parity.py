@@ -267,8 +267,8 @@ def test_hpe_exact_matches_oracle(dl):
     assert np.abs(got - ref).max() < 1e-14
 
 
-@pytest.mark.parametrize("hp_guess", [0, 1])
-def test_tsm_against_exact_loops(dl, hp_guess):
+@pytest.mark.parametrize("hp_guess,hpe_diff", [(0, 0), (1, 0), (1, 1)])
+def test_tsm_against_exact_loops(dl, hp_guess, hpe_diff):
     """Eq. estiTSM with an HP map converged to 1e-11 and an LP map converged to 1e-5:
     the estimate is the mean of the exact per-noise loops (dense inverse) over the HP
     and LP sets up to the LP error; the HP per-noise observables are exact (also when
@@ -281,7 +281,7 @@ def test_tsm_against_exact_loops(dl, hp_guess):
     try:
         prm = dl.dl_tsm_params(n_hp=n_hp, n_lp=n_lp, tol_hp=1e-11, tol_lp=1e-5, prec_hp_lo=dl.DL_F64,
                                prec_lp_lo=dl.DL_F32, delta_hp=0.1, block=4, seed=2000, p2max=1, with_deriv=0, hpe=1,
-                               max_iter=50000, chunk=8, hp_guess=hp_guess)
+                               max_iter=50000, chunk=8, hp_guess=hp_guess, hpe_diff=hpe_diff)
         np_ = len(dl.dl_momenta(1))
         out = np.zeros((3, dims[3], np_, 1, 4, 4), dtype=np.complex128)
         ohp = np.zeros((n_hp, 4))
