@@ -3,7 +3,7 @@
 
 Workload (32^3 x 64, eps 0.4, kappa 0.1612, a*mu 0.0055, antiperiodic in t):
 the Truncated Solver Method with N_HP = 24 high-precision (CG residual 1e-10,
-FP32 Krylov vectors, FP64 reliable updates at delta = 0.001) and N_LP = 500 low-precision
+FP32 Krylov vectors, FP64 reliable updates at delta = 1e-4) and N_LP = 500 low-precision
 (residual 1e-2, 16-bit fixed-point Krylov vectors) solves of the even-odd twisted-mass
 operator, batched 16 right-hand sides per launch, each solution contracted
 into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
@@ -38,7 +38,7 @@ DIMS = (32, 32, 32, 64)
 EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
 N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 16
 TOL_HP, TOL_LP = 1e-10, 1e-2
-DELTA_HP = 0.001  # reliable updates every three decades: each costs a high-precision operator application
+DELTA_HP = 1e-4  # reliable updates every four decades: each costs a high-precision operator application
 P2MAX = 9
 LINK_SEED, NOISE_SEED = 1002, 2002
 WORKLOAD = "tsm_32x32x32x64"
