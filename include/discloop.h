@@ -51,6 +51,7 @@ typedef enum {
   DL_ERR_CUDA = -2,   /* a CUDA call failed; the message names it */
   DL_ERR_OOM = -3,    /* device allocation failed */
   DL_ERR_STATE = -4,  /* call out of order (e.g. no gauge field loaded) */
+  DL_ERR_IO = -5,     /* a file could not be read or written, or failed its checks */
   DL_NOT_CONVERGED = 1, /* a solve reached max_iter; last iterate returned */
   DL_BREAKDOWN = 3      /* a CG scalar became zero, negative or non-finite */
 } dl_status;
@@ -394,6 +395,53 @@ typedef struct {
 
 dl_status dl_fgcr_solve(dl_ctx* ctx, dl_nn* precond, const dl_fgcr_params* params, int n,
                         const void* src, void* sol, int dtype, dl_fgcr_stats* stats);
+
+/* ---- base-2 storage of per-noise loops (App. A, "Binary storage system") ----
+ *
+ * Loops are averaged over noise vectors ("sources"), so it is enough to keep
+ * sums over groups of sources whose sizes are powers of two (Fig. St): the file
+ * of weight w = 2^k holds the elementwise sum of the loop arrays of sources
+ * w-1 .. 2w-2, counted from 0 in the order they were added (weight 1: source 0,
+ * weight 2: sources 1 and 2, weight 4: sources 3-6, ...).  The sum over a set of
+ * any n sources with n < 2^K, K the number of complete files, is the sum of the
+ * files whose weights are the set bits of n (n = 13: weights 1, 4 and 8), so N
+ * sources take O(log2 N) files.  A source is any array of n_values doubles, for
+ * example one noise vector's dl_contract output ([T][Np][nd][4][4] complex128 =
+ * 32*T*Np*nd doubles) copied to host memory.  These calls are host-only and need
+ * no GPU.
+ *
+ * Files: "<prefix>.<w>" for each complete group and "<prefix>.partial" for the
+ * group being filled when the writer is closed.  Format, integers little-endian:
+ * char[8] "DLLOOPB2", u32 version 1, u32 0, u64 weight, u64 sources summed (the
+ * weight, or fewer for .partial), u64 first source (weight - 1), u64 n_values,
+ * u64 FNV-1a-64 of the payload bytes, then n_values IEEE binary64 little-endian.
+ * Each file is written beside its name and renamed into place. */
+typedef struct dl_store dl_store;
+
+/* Message of the last failed dl_store_* call on this thread. */
+const char* dl_store_last_error(void);
+/* Open a writer of n_values-double sources under `prefix` (a path without
+ * suffix; its directory must exist).  resume = 0: a new store; DL_ERR_STATE if a
+ * file of a store already exists under the prefix.  resume = 1: continue the
+ * store found there (complete files 1, 2, 4, ... without a gap, then .partial),
+ * DL_ERR_IO if its files are inconsistent or n_values differs.  *st is NULL on
+ * failure; a writer is freed by dl_store_close. */
+dl_status dl_store_open(dl_store** st, const char* prefix, int64_t n_values, int resume);
+/* Add n_sources sources (host double[n_sources][n_values]) in order; every group
+ * that completes is written at once.  On DL_ERR_IO the sources before the
+ * failing write are kept and the write is retried by the next add or close. */
+dl_status dl_store_add(dl_store* st, const double* values, int64_t n_sources);
+/* Sources added so far, including those of a resumed store. */
+dl_status dl_store_count(const dl_store* st, int64_t* total);
+/* Write the incomplete group (if any) as .partial, remove a stale .partial
+ * otherwise, and free the writer (also when the write fails). */
+dl_status dl_store_close(dl_store* st);
+/* out (host double[n_values]) = sum over the set of n sources, read from the
+ * files of the set bits of n and checked (header, size, checksum); n = 0 gives
+ * zeros; DL_ERR_IO if a file is missing or fails a check. */
+dl_status dl_store_load(const char* prefix, int64_t n_values, int64_t n, double* out);
+/* The source indices of the set of n (if list != NULL, int64[n], ascending). */
+dl_status dl_store_sources(int64_t n, int64_t* list);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdiscloop.so")
 
-DL_OK, DL_ERR_ARG, DL_ERR_CUDA, DL_ERR_OOM, DL_ERR_STATE = 0, -1, -2, -3, -4
+DL_OK, DL_ERR_ARG, DL_ERR_CUDA, DL_ERR_OOM, DL_ERR_STATE, DL_ERR_IO = 0, -1, -2, -3, -4, -5
 DL_NOT_CONVERGED, DL_BREAKDOWN = 1, 3
 DL_F64, DL_F32, DL_F16, DL_BF16, DL_F64_IEEE = 0, 1, 2, 3, 5
 DL_C128, DL_C64 = 0, 1
@@ -120,6 +120,13 @@ _SIGS = {
                               C.c_void_p]),
     "dl_fgcr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(dl_fgcr_params), C.c_int, C.c_void_p, C.c_void_p,
                                 C.c_int, C.POINTER(dl_fgcr_stats)]),
+    "dl_store_last_error": (C.c_char_p, []),
+    "dl_store_open": (C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_int64, C.c_int]),
+    "dl_store_add": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "dl_store_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "dl_store_close": (C.c_int, [C.c_void_p]),
+    "dl_store_load": (C.c_int, [C.c_char_p, C.c_int64, C.c_int64, C.c_void_p]),
+    "dl_store_sources": (C.c_int, [C.c_int64, C.c_void_p]),
 }
 
 
@@ -349,3 +356,64 @@ def dl_fgcr_solve(ctx, nn, params: dl_fgcr_params, n, src, sol, dtype=DL_C128):
     st = _check(ctx, lib().dl_fgcr_solve(ctx, nn["h"] if nn else None, C.byref(params), int(n), _ptr(src), _ptr(sol),
                                          int(dtype), C.byref(stats)))
     return st, stats
+
+
+# ---- base-2 storage of per-noise loops (host only) ----
+
+def _check_store(status):
+    if status < 0:
+        raise DLError(status, lib().dl_store_last_error().decode())
+    return status
+
+
+def _as_doubles(values):
+    """A host array of float64 or complex128 as a contiguous float64 view."""
+    a = np.ascontiguousarray(values)
+    if a.dtype == np.complex128:
+        return a.view(np.float64)
+    if a.dtype != np.float64:
+        raise TypeError("sources must be float64 or complex128 host arrays")
+    return a
+
+
+def dl_store_last_error():
+    return lib().dl_store_last_error().decode()
+
+
+def dl_store_open(prefix, n_values, resume=0):
+    """Writer handle {"h", "n_values"} for sources of n_values doubles (a complex128
+    value counts as two)."""
+    h = C.c_void_p()
+    _check_store(lib().dl_store_open(C.byref(h), os.fsencode(prefix), int(n_values), int(resume)))
+    return {"h": h.value, "n_values": int(n_values)}
+
+
+def dl_store_add(st, values):
+    """values: host float64/complex128 array holding whole sources, in order."""
+    a = _as_doubles(values)
+    if a.size % st["n_values"]:
+        raise ValueError(f"{a.size} doubles is not a whole number of sources of {st['n_values']}")
+    return _check_store(lib().dl_store_add(st["h"], a.ctypes.data, a.size // st["n_values"]))
+
+
+def dl_store_count(st):
+    n = C.c_int64()
+    _check_store(lib().dl_store_count(st["h"], C.byref(n)))
+    return n.value
+
+
+def dl_store_close(st):
+    h, st["h"] = st["h"], None
+    return _check_store(lib().dl_store_close(h))
+
+
+def dl_store_load(prefix, n_values, n):
+    out = np.zeros(int(n_values), dtype=np.float64)
+    _check_store(lib().dl_store_load(os.fsencode(prefix), int(n_values), int(n), out.ctypes.data))
+    return out
+
+
+def dl_store_sources(n):
+    out = np.zeros(int(n), dtype=np.int64)
+    _check_store(lib().dl_store_sources(int(n), out.ctypes.data if n else None))
+    return out

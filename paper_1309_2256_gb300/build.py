@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdiscloop.so")
-SOURCES = ["dl_dslash.cu", "dl_blas.cu", "dl_layout.cu", "dl_contract.cu", "dl_network.cu", "dl_learned.cu", "dl_api.cu"]
+SOURCES = ["dl_dslash.cu", "dl_blas.cu", "dl_layout.cu", "dl_contract.cu", "dl_network.cu", "dl_learned.cu", "dl_api.cu",
+           "dl_store.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # extra nvcc flags, e.g. DL_NVCC_EXTRA="-DDL_MINB=3" to build a variant of the stencil
@@ -41,7 +42,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
