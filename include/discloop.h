@@ -121,6 +121,16 @@ dl_status dl_set_params(dl_ctx* ctx, double kappa, double amu);
  * Lea & Flood (2014): state = seed + (counter+1)*0x9E3779B97F4A7C15. */
 dl_status dl_noise_z4(dl_ctx* ctx, uint64_t seed, uint64_t first_index, int n,
                       void* out, int dtype, int quadrant);
+/* Time-diluted noise (Sec. 2.3, time dilution and coherent sources): the fields
+ * of dl_noise_z4 with every time slice t != t0 (mod dt) set to zero, so that a
+ * source fills the slices t0, t0 + dt, ... only (dt = T: one slice; smaller dt:
+ * coherent sources on several slices dt apart).  The dt sources t0 = 0 .. dt-1
+ * of one noise index sum to its dl_noise_z4 field.  Solving for such a source
+ * and contracting it with dl_contract (DL_EST_STANDARD, or DL_EST_HPE plus
+ * dl_hpe_exact times X*Y*Z at zero momentum on each kept slice) gives loops that
+ * vanish off the kept slices.  Needs 1 <= dt <= T and 0 <= t0 < dt. */
+dl_status dl_noise_z4_tdil(dl_ctx* ctx, uint64_t seed, uint64_t first_index, int n,
+                           void* out, int dtype, int quadrant, int t0, int dt);
 
 /* ---- operators (App. A) -------------------------------------------------- */
 

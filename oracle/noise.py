@@ -13,6 +13,13 @@ definition: state_n = seed + (n + 1) * 0x9E3779B97F4A7C15 (mod 2^64), then
 z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27; z *= 0x94D049BB133111EB;
 z ^= z >> 31.  Counter n = (r * V + lex) * 12 + 3 * spin + colour.
 Bit 0 of the output gives s1 (0 -> +1), bit 1 gives s2.
+
+Time dilution (Sec. 2.3): the noise space is split into subspaces and a source
+fills one of them.  With the subspaces taken as sets of time slices, a source
+keeps the entries of a full noise vector on the slices t = t0 (mod dt) and is
+zero elsewhere: dt = T gives one slice per source, a smaller dt the coherent
+sources of several far-apart slices.  The dt sources t0 = 0 .. dt-1 of one noise
+vector sum to it (the direct sum of the subspaces).
 """
 from __future__ import annotations
 
@@ -53,3 +60,13 @@ def z4_noise(dims, seed: int, r: int, quadrant: bool = False) -> np.ndarray:
     s1 = 1.0 - 2.0 * b0
     s2 = 1.0 - 2.0 * b1
     return (s1 + 1j * s2) / np.sqrt(2.0)
+
+
+def time_diluted(eta: np.ndarray, t0: int, dt: int) -> np.ndarray:
+    """eta ([T][Z][Y][X][4][3]) on the time slices t = t0 (mod dt), zero elsewhere (Sec. 2.3)."""
+    T = eta.shape[0]
+    if not (1 <= dt <= T and 0 <= t0 < dt):
+        raise ValueError("need 1 <= dt <= T and 0 <= t0 < dt")
+    out = np.zeros_like(eta)
+    out[t0::dt] = eta[t0::dt]
+    return out

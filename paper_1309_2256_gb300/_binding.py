@@ -89,6 +89,8 @@ _SIGS = {
     "dl_load_gauge": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int]),
     "dl_set_params": (C.c_int, [C.c_void_p, C.c_double, C.c_double]),
     "dl_noise_z4": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int]),
+    "dl_noise_z4_tdil": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                   C.c_int]),
     "dl_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "dl_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(dl_solve_params),
                            C.POINTER(dl_solve_stats)]),
@@ -209,6 +211,11 @@ def dl_set_params(ctx, kappa, amu):
 
 def dl_noise_z4(ctx, seed, first_index, n, out, dtype=DL_C128, quadrant=0):
     return _check(ctx, lib().dl_noise_z4(ctx, int(seed), int(first_index), int(n), _ptr(out), int(dtype), int(quadrant)))
+
+
+def dl_noise_z4_tdil(ctx, seed, first_index, n, out, t0, dt, dtype=DL_C128, quadrant=0):
+    return _check(ctx, lib().dl_noise_z4_tdil(ctx, int(seed), int(first_index), int(n), _ptr(out), int(dtype),
+                                              int(quadrant), int(t0), int(dt)))
 
 
 def dl_apply(ctx, op, prec, flavour, n, inp, aux, out, dtype=DL_C128):

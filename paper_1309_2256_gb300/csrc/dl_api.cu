@@ -1008,6 +1008,34 @@ dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, voi
   return leave(c);
 }
 
+// Time dilution (Sec. 2.3): the noise of dl_noise_z4 on the slices t = t0 (mod dt), zero
+// elsewhere.  The natural layout [n][T][Z][Y][X][4][3] keeps each time slice of each column
+// contiguous, so the cleared slices are byte ranges of `out`: consecutive ones (also across
+// columns) are merged and cleared by one memset each.
+dl_status dl_noise_z4_tdil(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant,
+                           int t0, int dt) {
+  dl_status s;
+  if ((s = check_ctx(c, false)) != DL_OK) return s;
+  const int T = c->dims[3];
+  if (dt < 1 || dt > T || t0 < 0 || t0 >= dt)
+    return fail(c, DL_ERR_ARG, "dl_noise_z4_tdil: need 1 <= dt <= T and 0 <= t0 < dt");
+  if ((s = dl_noise_z4(c, seed, first_index, n, out, dtype, quadrant)) != DL_OK) return s;
+  if ((s = enter(c)) != DL_OK) return s;
+  const size_t slice = (size_t)c->dims[0] * c->dims[1] * c->dims[2] * 12 * (dtype == DL_C128 ? 16 : 8);
+  char* base = static_cast<char*>(out);
+  const long long nslices = (long long)n * T;  // out holds exactly n * T slices
+  long long run = -1;                           // first slice of the run being cleared
+  for (long long j = 0; j <= nslices; ++j) {
+    const bool clear = j < nslices && (int)(j % T) % dt != t0;
+    if (clear && run < 0) run = j;
+    if (!clear && run >= 0) {
+      CK(cudaMemsetAsync(base + (size_t)run * slice, 0, (size_t)(j - run) * slice, c->st));
+      run = -1;
+    }
+  }
+  return leave(c);
+}
+
 dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux, void* out, int dtype) {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
