@@ -558,13 +558,53 @@ def batch_case(args):
     print(json.dumps(res))
 
 
+def mass_case(args):
+    """Cost ratio R_HP/LP of the TSM versus the valence twisted mass (Sec. 4, Table compRatios):
+    16^3 x 32 (eps 0.4, kappa 0.161), one-end and generalised one-end loops, per a*mu the cost
+    of one noise vector's loops from an HP solve (1e-10, from zero) over that from an LP solve
+    (1e-2), each with its contractions; local only and with the one-derivative loops.  The
+    masses are a light, a strange-like and a charm-like choice (the paper does not print its
+    strange and charm values)."""
+    import torch
+
+    import paper_1309_2256_gb300 as dl
+    import synth
+    dims = (16, 16, 16, 32)
+    kappa = 0.161
+    masses = [float(m) for m in args.masses.split(",")]
+    n_hp, n_lp = 16, 48
+    ctx = dl.dl_create(dims, 0, torch.cuda.current_stream())
+    dl.dl_load_gauge(ctx, synth.gauge_links(dims, 0.4, 1001), -1.0, 12, 12)
+    rows = []
+    for amu in masses:
+        dl.dl_set_params(ctx, kappa, amu)
+        row = {"amu": amu}
+        for deriv in (0, 1):
+            prm = dl.dl_tsm_params(n_hp=n_hp, n_lp=n_lp, tol_hp=1e-10, tol_lp=1e-2, prec_hp_lo=dl.DL_F32,
+                                   prec_lp_lo=dl.DL_F16, delta_hp=DELTA_HP, block=16, seed=3001, p2max=4,
+                                   with_deriv=deriv, hpe=0, max_iter=200000, chunk=32, hp_guess=0, hpe_diff=0)
+            for rep in range(2):  # the first run builds this mass's graphs and workspaces
+                st, info = dl.dl_tsm_run(ctx, prm, None, None, None, None)
+            t_hp = info.seconds_hp / n_hp
+            t_lp = info.seconds_lp / (n_hp + n_lp)
+            t_c = info.seconds_contract / (2 * n_hp + n_lp)
+            key = "one_deriv" if deriv else "local"
+            row[key] = {"r_hp_lp": (t_hp + t_c) / (t_lp + t_c), "sec_hp_solve": t_hp, "sec_lp_solve": t_lp,
+                        "sec_contract_per_solution": t_c, "iters_hp": info.iters_hp / n_hp,
+                        "iters_lp": info.iters_lp / (n_hp + n_lp), "not_converged": info.not_converged}
+        rows.append(row)
+    dl.dl_destroy(ctx)
+    print(json.dumps({"case": "mass_sweep", "data": "synthetic", "lattice": list(dims), "kappa": kappa,
+                      "n_hp": n_hp, "n_lp": n_lp, "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default=None, choices=["stencil", "contract", "learned", "batch"],
+    ap.add_argument("--case", default=None, choices=["stencil", "contract", "learned", "batch", "mass"],
                     help="small profiling case instead of the benchmark (for ncu)")
     ap.add_argument("--delta-hp", type=float, default=DELTA_HP,
                     help="reliable-update trigger of the high-precision solves")
@@ -576,7 +616,11 @@ def main():
     ap.add_argument("--fgcr-max-iter", type=int, default=600, help="learned case: FGCR iterations per solve")
     ap.add_argument("--batch", type=int, default=4, help="learned case: pairs per Adam step")
     ap.add_argument("--lr", type=float, default=1e-3, help="learned case: Adam learning rate")
+    ap.add_argument("--masses", default="0.0055,0.02,0.2", help="mass case: valence a*mu values")
     args = ap.parse_args()
+    if args.case == "mass":
+        mass_case(args)
+        return
     if args.case == "learned":
         learned_case(args)
         return
