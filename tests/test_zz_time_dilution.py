@@ -70,7 +70,7 @@ def test_time_diluted_loops_standard_and_hpe(dl):
         eta = torch.empty((n,) + dims[::-1] + (4, 3), dtype=torch.complex128, device="cuda")
         dl.dl_noise_z4_tdil(ctx, 2100, 0, n, eta, t0, dt)
         sol = torch.empty_like(eta)
-        prm = dl.dl_solve_params(tol=1e-10, max_iter=50000, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.1,
+        prm = dl.dl_solve_params(tol=1e-10, max_iter=50000, prec_hi=dl.DL_F64, prec_lo=dl.DL_F64, delta=0.0,
                                  flavour=1, chunk=8)
         st, stats = dl.dl_solve(ctx, eta, sol, n, dl.DL_C128, prm)
         assert st == 0
