@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <string>
 #include <vector>
@@ -468,6 +469,7 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
   CGState h;
   if ((s = download_state(c, n, h)) != DL_OK) return s;
   const double tol2_ = prm.tol * prm.tol;
+  std::vector<int> nonfinite(n, 0);  // NaN or Inf in |b|^2 or the initial residual: not iterated
   for (int i = 0; i < n; ++i) {
     const double rr0 = h.S[DL_S_RR0 * DL_NCMAX + i];
     const double rr = x_init ? h.S[DL_S_TMP * DL_NCMAX + i] : rr0;
@@ -475,6 +477,10 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     h.S[DL_S_MAXR * DL_NCMAX + i] = sqrt(rr);
     h.active[i] = (rr0 > 0.0 && rr > tol2_ * rr0) ? 1 : 0;
     h.flags[i] = 0;
+    if (!std::isfinite(rr0) || !std::isfinite(rr)) {
+      h.active[i] = 0;
+      nonfinite[i] = 1;
+    }
   }
   h.iters.assign(n, 0);
   CK(cudaMemcpyAsync(c->iters, h.iters.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
@@ -494,6 +500,11 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
   int n_rel = 0;
   auto t0 = std::chrono::steady_clock::now();
   bool breakdown = false;
+  for (int i = 0; i < n; ++i)
+    if (nonfinite[i]) {
+      breakdown = true;
+      c->err = "non-finite source or initial residual in column " + std::to_string(i);
+    }
   // a breakdown in low-precision arithmetic restarts the column from its true residual
   // (p = r after a reliable update), at most 8 times, when reliable updates are enabled
   std::vector<int> restarts(n, 0);
@@ -665,6 +676,10 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     stats->max_iters = maxit;
     stats->seconds = secs;
   }
+  for (int i = 0; i < n; ++i)
+    if (nonfinite[i]) resid[i] = std::numeric_limits<double>::quiet_NaN();
+  if (stats)
+    for (int i = 0; i < n && i < DL_MAX_RHS; ++i) stats->resid[i] = resid[i];
   if (resid_out)
     for (int i = 0; i < n; ++i) resid_out[i] = resid[i];
   c->last_iters.assign(h.iters.begin(), h.iters.begin() + n);
