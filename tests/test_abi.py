@@ -48,4 +48,52 @@ def test_bad_arguments_are_rejected_without_gpu():
     assert h.dl_create(C.byref(out), odd, 0, None) == dl.DL_ERR_ARG
     assert h.dl_solve(None, None, None, 1, 0, None, None) == dl.DL_ERR_ARG
     assert h.dl_tsm_run(None, None, None, None, None, None, None) == dl.DL_ERR_ARG
-    assert np.isfinite(1.0)
+
+
+# every call that takes a context or network handle, with that handle NULL and every
+# other pointer NULL: a status, never a crash (no GPU needed)
+NULL_HANDLE_CALLS = {
+    "dl_set_stream": (None, None),
+    "dl_load_gauge": (None, None, 0, -1.0, 12, 8),
+    "dl_set_params": (None, 0.1, 0.01),
+    "dl_noise_z4": (None, 1, 0, 1, None, 0, 0),
+    "dl_noise_z4_tdil": (None, 1, 0, 1, None, 0, 0, 0, 1),
+    "dl_apply": (None, 0, 0, 1, 1, None, None, None, 0),
+    "dl_apply_noalloc": (None, 0, 0, 1, 1, None, None, None, 0),
+    "dl_solve": (None, None, None, 1, 0, None, None),
+    "dl_contract": (None, 0, None, None, 1, 0, 0, 0, None, 0),
+    "dl_hpe_exact": (None, 1, None),
+    "dl_tsm_run": (None, None, None, None, None, None, None),
+    "dl_load_gauge_lat": (None, 0, None, 0, -1.0, 12, 12),
+    "dl_set_params_lat": (None, 0, 0.1, 0.01),
+    "dl_batch_loops": (None, None, None, None, None),
+    "dl_profile": (None, 1, None),
+    "dl_nn_create": (None, 2, 4, 3, None),
+    "dl_nn_set_tensor_cores": (None, 1),
+    "dl_nn_set_weights": (None, None),
+    "dl_nn_get_weights": (None, None),
+    "dl_nn_apply": (None, 1, None, None, 0),
+    "dl_nn_apply_adjoint": (None, 1, None, None, 0),
+    "dl_nn_loss_grad": (None, 1, None, None, 0, None, None),
+    "dl_nn_train": (None, None, 1, None, None, 0, None),
+    "dl_fgcr_solve": (None, None, None, 1, None, None, 0, None),
+    "dl_create_multi": (None, 1, None, 0, None),
+    "dl_store_add": (None, None, 1),
+    "dl_store_count": (None, None),
+}
+# calls without a handle argument, or whose NULL handle is a no-op by definition
+NO_HANDLE = {"dl_create", "dl_momenta", "dl_kernel_launches", "dl_destroy", "dl_nn_destroy", "dl_last_error",
+             "dl_nn_weight_count", "dl_store_last_error", "dl_store_open", "dl_store_close", "dl_store_load",
+             "dl_store_sources"}
+
+
+def test_null_handles_are_rejected():
+    import paper_1309_2256_gb300 as dl
+    h = dl.lib()
+    assert set(NULL_HANDLE_CALLS) | NO_HANDLE == _declared()
+    for name, args in NULL_HANDLE_CALLS.items():
+        assert getattr(h, name)(*args) == dl.DL_ERR_ARG, name
+    h.dl_destroy(None)
+    h.dl_nn_destroy(None)
+    assert h.dl_nn_weight_count(None) == 0
+    assert h.dl_last_error(None) is not None
