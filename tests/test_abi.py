@@ -3,7 +3,6 @@ exports every function include/discloop.h declares; host-only logic matches the 
 import os
 import re
 
-import numpy as np
 
 from oracle import lattice
 
