@@ -3,7 +3,6 @@ exports every function include/discloop.h declares; host-only logic matches the 
 import os
 import re
 
-
 from oracle import lattice
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
