@@ -1,7 +1,6 @@
 """Pins of the oracle's parallel-transport network (CPU only): finite-difference
 gradients, gauge equivariance, and a closed form built from the operator module."""
 import numpy as np
-import pytest
 
 import synth
 from oracle import loops, network, noise
