@@ -885,15 +885,15 @@ static dl_status create_ctx(dl_ctx** out, int nlat, const int* dims, int device,
   return DL_OK;
 }
 
-dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stream) {
+dl_status dl_create(dl_ctx** out, const int dims[4], int device, void* cuda_stream) try {
   return create_ctx(out, 1, dims, device, cuda_stream);
-}
+} DL_CATCH(nullptr)
 
-dl_status dl_create_multi(dl_ctx** out, int nlat, const int* dims, int device, void* cuda_stream) {
+dl_status dl_create_multi(dl_ctx** out, int nlat, const int* dims, int device, void* cuda_stream) try {
   return create_ctx(out, nlat, dims, device, cuda_stream);
-}
+} DL_CATCH(nullptr)
 
-void dl_destroy(dl_ctx* c) {
+void dl_destroy(dl_ctx* c) try {
   if (!c) return;
   cudaSetDevice(c->dev);
   if (c->st) cudaStreamSynchronize(c->st);
@@ -914,18 +914,19 @@ void dl_destroy(dl_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
+} catch (...) {
 }
 
 const char* dl_last_error(const dl_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-dl_status dl_set_stream(dl_ctx* c, void* s) {
+dl_status dl_set_stream(dl_ctx* c, void* s) try {
   if (!c) return DL_ERR_ARG;
   c->user = (cudaStream_t)s;
   return DL_OK;
-}
+} DL_CATCH(c)
 
 dl_status dl_load_gauge_lat(dl_ctx* c, int lat, const double* links, int on_device, double t_boundary, int recon_f32,
-                            int recon_f16) {
+                            int recon_f16) try {
   if (!c || !links || lat < 0 || lat >= (int)c->lats.size()) return DL_ERR_ARG;
   if (!(recon_f32 == 12 || recon_f32 == 8 || recon_f32 == 18)) return fail(c, DL_ERR_ARG, "recon_f32 must be 18, 12 or 8");
   if (!(recon_f16 == 12 || recon_f16 == 8)) return fail(c, DL_ERR_ARG, "recon_f16 must be 12 or 8");
@@ -980,13 +981,13 @@ dl_status dl_load_gauge_lat(dl_ctx* c, int lat, const double* links, int on_devi
   for (auto& Lx : c->lats) c->has_gauge = c->has_gauge && Lx.has_gauge;
   invalidate_graphs(c);
   return leave(c);
-}
+} DL_CATCH(c)
 
-dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_boundary, int recon_f32, int recon_f16) {
+dl_status dl_load_gauge(dl_ctx* c, const double* links, int on_device, double t_boundary, int recon_f32, int recon_f16) try {
   return dl_load_gauge_lat(c, 0, links, on_device, t_boundary, recon_f32, recon_f16);
-}
+} DL_CATCH(c)
 
-dl_status dl_set_params_lat(dl_ctx* c, int lat, double kappa, double amu) {
+dl_status dl_set_params_lat(dl_ctx* c, int lat, double kappa, double amu) try {
   if (!c || lat < 0 || lat >= (int)c->lats.size()) return DL_ERR_ARG;
   if (!(kappa > 0.0) || !std::isfinite(kappa) || !std::isfinite(amu)) return fail(c, DL_ERR_ARG, "bad kappa/amu");
   c->lats[lat].kappa = kappa;
@@ -996,18 +997,18 @@ dl_status dl_set_params_lat(dl_ctx* c, int lat, double kappa, double amu) {
     c->amu = amu;
   }
   return DL_OK;
-}
+} DL_CATCH(c)
 
-dl_status dl_set_params(dl_ctx* c, double kappa, double amu) {
+dl_status dl_set_params(dl_ctx* c, double kappa, double amu) try {
   if (!c) return DL_ERR_ARG;
   for (int l = 0; l < (int)c->lats.size(); ++l) {
     dl_status s = dl_set_params_lat(c, l, kappa, amu);
     if (s != DL_OK) return s;
   }
   return DL_OK;
-}
+} DL_CATCH(c)
 
-dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant) {
+dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant) try {
   if (!c || !out || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64)) return DL_ERR_ARG;
   dl_status s;
   if ((s = check_ctx(c, false)) != DL_OK) return s;
@@ -1021,14 +1022,14 @@ dl_status dl_noise_z4(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, voi
   CK(dl::unpack(B, prec, 0, out, e->ref(), dtype, c->st));
   CK(dl::unpack(B, prec, 1, out, o->ref(), dtype, c->st));
   return leave(c);
-}
+} DL_CATCH(c)
 
 // Time dilution (Sec. 2.3): the noise of dl_noise_z4 on the slices t = t0 (mod dt), zero
 // elsewhere.  The natural layout [n][T][Z][Y][X][4][3] keeps each time slice of each column
 // contiguous, so the cleared slices are byte ranges of `out`: consecutive ones (also across
 // columns) are merged and cleared by one memset each.
 dl_status dl_noise_z4_tdil(dl_ctx* c, uint64_t seed, uint64_t first_index, int n, void* out, int dtype, int quadrant,
-                           int t0, int dt) {
+                           int t0, int dt) try {
   dl_status s;
   if ((s = check_ctx(c, false)) != DL_OK) return s;
   const int T = c->dims[3];
@@ -1049,9 +1050,9 @@ dl_status dl_noise_z4_tdil(dl_ctx* c, uint64_t seed, uint64_t first_index, int n
     }
   }
   return leave(c);
-}
+} DL_CATCH(c)
 
-dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux, void* out, int dtype) {
+dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux, void* out, int dtype) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec_rank(prec) < 0 ||
@@ -1129,10 +1130,10 @@ dl_status dl_apply(dl_ctx* c, int op, int prec, int f, int n, const void* in, co
   CK(dl::unpack(B, prec, 0, out, oe->ref(), dtype, c->st));
   CK(dl::unpack(B, prec, 1, out, oo->ref(), dtype, c->st));
   return leave(c);
-}
+} DL_CATCH(c)
 
 dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, const dl_solve_params* prm,
-                   dl_solve_stats* stats) {
+                   dl_solve_stats* stats) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!src || !sol || !prm || n < 1 || n > DL_MAX_RHS || (dtype != DL_C128 && dtype != DL_C64))
@@ -1199,9 +1200,9 @@ dl_status dl_solve(dl_ctx* c, const void* src, void* sol, int n, int dtype, cons
   dl_status ls = leave(c);
   if (ls != DL_OK) return ls;
   return rs;
-}
+} DL_CATCH(c)
 
-dl_status dl_profile(dl_ctx* c, int enable, double* out) {
+dl_status dl_profile(dl_ctx* c, int enable, double* out) try {
   if (!c) return DL_ERR_ARG;
   if (out) {
     for (int k = 0; k < 4; ++k)
@@ -1220,11 +1221,11 @@ dl_status dl_profile(dl_ctx* c, int enable, double* out) {
     memset(c->prof_items, 0, sizeof(c->prof_items));
   }
   return DL_OK;
-}
+} DL_CATCH(c)
 
 long long dl_kernel_launches(void) { return g_launches.load(); }
 
-dl_status dl_momenta(int p2max, int* count, int* list) {
+dl_status dl_momenta(int p2max, int* count, int* list) try {
   if (!count || p2max < 0 || p2max > 64) return DL_ERR_ARG;
   int m = mom_extent(p2max);
   int k = 0;
@@ -1241,10 +1242,10 @@ dl_status dl_momenta(int p2max, int* count, int* list) {
         }
   *count = k;
   return DL_OK;
-}
+} DL_CATCH(nullptr)
 
 dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int with_deriv, int p2max,
-                      double* out, int accumulate) {
+                      double* out, int accumulate) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!sol || !out || n < 1 || n > DL_MAX_RHS || est < 0 || est > 3 || p2max < 0 || p2max > 64 ||
@@ -1283,9 +1284,9 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
                              accumulate)) != DL_OK)
     return s;
   return leave(c);
-}
+} DL_CATCH(c)
 
-dl_status dl_hpe_exact(dl_ctx* c, int flavour, double* out16) {
+dl_status dl_hpe_exact(dl_ctx* c, int flavour, double* out16) try {
   if (!c || !out16 || (flavour != 1 && flavour != -1)) return DL_ERR_ARG;
   dl_status s;
   if ((s = enter(c)) != DL_OK) return s;
@@ -1293,10 +1294,10 @@ dl_status dl_hpe_exact(dl_ctx* c, int flavour, double* out16) {
   CK(cudaMemcpyAsync(out16, c->misc, sizeof(double2) * 16, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   return leave(c);
-}
+} DL_CATCH(c)
 
 dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double* obs_hp, double* obs_lp_pair,
-                     double* obs_lp, dl_tsm_info* info) {
+                     double* obs_lp, dl_tsm_info* info) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!prm || prm->n_hp < 0 || prm->n_lp < 0 || prm->n_hp + prm->n_lp < 1 || prm->block < 1 || prm->block > DL_MAX_RHS ||
@@ -1486,9 +1487,9 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
   }
   if ((s = leave(c)) != DL_OK) return s;
   return any_nc ? fail(c, DL_NOT_CONVERGED, "a TSM solve hit max_iter") : DL_OK;
-}
+} DL_CATCH(c)
 
-dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, void* sol, dl_batch_info* info) {
+dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, void* sol, dl_batch_info* info) try {
   if (!c || !prm) return DL_ERR_ARG;
   const int nl = (int)c->lats.size();
   for (auto& L : c->lats)
@@ -1621,7 +1622,7 @@ dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, v
   if (info) *info = inf;
   if ((s = leave(c)) != DL_OK) return s;
   return nc ? fail(c, DL_NOT_CONVERGED, "dl_batch_loops: a solve hit max_iter") : DL_OK;
-}
+} DL_CATCH(c)
 
 }  // extern "C"
 
@@ -1661,7 +1662,7 @@ cudaError_t noalloc_scratch(int dev, unsigned char** out) {
 }  // namespace
 
 extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n, const void* in, const void* aux,
-                                      void* out, int dtype) {
+                                      void* out, int dtype) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!in || !out || n < 1 || n > DL_MAX_RHS || (f != 1 && f != -1) || prec_rank(prec) < 0 ||
@@ -1750,4 +1751,4 @@ extern "C" dl_status dl_apply_noalloc(dl_ctx* c, int op, int prec, int f, int n,
   CK(dl::unpack(B, prec, 0, out, oe, dtype, c->st));
   CK(dl::unpack(B, prec, 1, out, oo, dtype, c->st));
   return leave(c);
-}
+} DL_CATCH(c)

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -126,4 +127,26 @@ cudaError_t colsum(dl_ctx* c, const Batch& B, int slot);
 // x = N(eta) column by column with the learned map (FP32 fields of a single-lattice block)
 dl_status nn_map_block(dl_nn* nn, dl_ctx* c, const Batch& B, Field* ee, Field* eo, Field* xe, Field* xo);
 
+// An exception raised by host-side bookkeeping inside an entry point (a failed host
+// allocation in a std::vector, std::map or std::string) becomes a status and a
+// message; nothing is thrown across the C boundary.
+inline dl_status host_exception(dl_ctx* c, dl_status s) noexcept {
+  if (c) {
+    try {
+      c->err = s == DL_ERR_OOM ? "host allocation failed" : "unexpected host exception";
+    } catch (...) {
+    }
+  }
+  return s;
+}
+
 }  // namespace dlh
+
+// Handler of the function-try-block around the body of every entry point.
+#define DL_CATCH(ctx_expr)                                                   \
+  catch (const std::bad_alloc&) {                                           \
+    return dlh::host_exception((ctx_expr), DL_ERR_OOM);                     \
+  }                                                                          \
+  catch (...) {                                                              \
+    return dlh::host_exception((ctx_expr), DL_ERR_STATE);                   \
+  }

@@ -255,7 +255,7 @@ dl_status nn_map_block(dl_nn* nn, dl_ctx* c, const Batch& B, Field* ee, Field* e
 
 extern "C" {
 
-dl_status dl_nn_create(dl_ctx* c, int n_layers, int channels, int act_prec, dl_nn** out) {
+dl_status dl_nn_create(dl_ctx* c, int n_layers, int channels, int act_prec, dl_nn** out) try {
   dl_status s;
   if (!out) return DL_ERR_ARG;
   *out = nullptr;
@@ -303,9 +303,9 @@ dl_status dl_nn_create(dl_ctx* c, int n_layers, int channels, int act_prec, dl_n
   }
   *out = nn;
   return DL_OK;
-}
+} DL_CATCH(c)
 
-void dl_nn_destroy(dl_nn* nn) {
+void dl_nn_destroy(dl_nn* nn) try {
   if (!nn) return;
   if (nn->c) {
     cudaSetDevice(nn->c->dev);
@@ -320,19 +320,20 @@ void dl_nn_destroy(dl_nn* nn) {
   cudaFree(nn->tcB);
   cudaFree(nn->tc_err);
   delete nn;
+} catch (...) {
 }
 
 long long dl_nn_weight_count(const dl_nn* nn) { return nn ? (long long)nn->nw : 0; }
 
-dl_status dl_nn_set_tensor_cores(dl_nn* nn, int enable) {
+dl_status dl_nn_set_tensor_cores(dl_nn* nn, int enable) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   if (enable && nn->act != PBF) return fail(nn->c, DL_ERR_ARG, "the tensor-core forward needs bfloat16 activations");
   nn->use_tc = enable != 0;
   nn->tc_dirty = true;
   return DL_OK;
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
-dl_status dl_nn_set_weights(dl_nn* nn, const float* w) {
+dl_status dl_nn_set_weights(dl_nn* nn, const float* w) try {
   if (!valid_nn(nn) || !w) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   dl_status s;
@@ -344,9 +345,9 @@ dl_status dl_nn_set_weights(dl_nn* nn, const float* w) {
   CK(cudaStreamSynchronize(c->st));
   nn->adam_t = 0;
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
-dl_status dl_nn_get_weights(dl_nn* nn, float* w) {
+dl_status dl_nn_get_weights(dl_nn* nn, float* w) try {
   if (!valid_nn(nn) || !w) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   dl_status s;
@@ -354,9 +355,9 @@ dl_status dl_nn_get_weights(dl_nn* nn, float* w) {
   CK(cudaMemcpyAsync(w, nn->W, sizeof(float2) * nn->nw, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
-dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype) {
+dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   if (!in || !out || n < 1 || (dtype != DL_C128 && dtype != DL_C64)) return fail(c, DL_ERR_ARG, "dl_nn_apply: bad argument");
@@ -374,9 +375,9 @@ dl_status dl_nn_apply(dl_nn* nn, int n, const void* in, void* out, int dtype) {
   }
   if ((s = check_tc(nn)) != DL_OK) return s;
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
-dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int dtype) {
+dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int dtype) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   if (!in || !out || n < 1 || (dtype != DL_C128 && dtype != DL_C64))
@@ -395,9 +396,9 @@ dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int d
       CK(dl::unpack(B1, nn->act, p, (char*)out + off, p ? G.o[0]->ref() : G.e[0]->ref(), dtype, c->st));
   }
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
-dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int dtype, double* loss, float* grad) {
+dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int dtype, double* loss, float* grad) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   if (!eta || !s || n < 1 || (dtype != DL_C128 && dtype != DL_C64)) return fail(c, DL_ERR_ARG, "dl_nn_loss_grad: bad argument");
@@ -420,10 +421,10 @@ dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int 
   if (loss) *loss = L;
   if ((st = check_tc(nn)) != DL_OK) return st;
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
 dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, const void* eta, const void* s, int dtype,
-                      double* loss_hist) {
+                      double* loss_hist) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   if (!prm || !eta || !s || n_pairs < 1 || prm->steps < 0 || prm->batch < 1 || prm->batch > n_pairs ||
@@ -477,10 +478,10 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, con
   CK(cudaStreamSynchronize(c->st));
   if ((st = check_tc(nn)) != DL_OK) return st;
   return leave(c);
-}
+} DL_CATCH((nn ? nn->c : nullptr))
 
 dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, const void* src, void* sol, int dtype,
-                        dl_fgcr_stats* stats) {
+                        dl_fgcr_stats* stats) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!prm || !src || !sol || n < 1 || n > DL_MAX_RHS || !(prm->tol > 0.0) || prm->max_iter < 1 || prm->restart < 1 ||
@@ -660,6 +661,6 @@ dl_status dl_fgcr_solve(dl_ctx* c, dl_nn* nn, const dl_fgcr_params* prm, int n, 
   if (stats) *stats = st;
   if ((s = leave(c)) != DL_OK) return s;
   return any_nc ? fail(c, DL_NOT_CONVERGED, "dl_fgcr_solve: max_iter reached") : DL_OK;
-}
+} DL_CATCH(c)
 
 }  // extern "C"
