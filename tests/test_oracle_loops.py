@@ -245,3 +245,21 @@ def test_tsm_unbiased_and_exact_algebra():
     # the truncated map alone is biased: its plain mean misses the exact trace
     f_lp_only = np.mean([f_of(noise.z4_noise(dims, 72, i), lp(noise.z4_noise(dims, 72, i))) for i in range(200)])
     assert abs(f_lp_only - exact) > abs(ests.mean() - exact)
+
+
+def test_tsm_error_matches_the_spread_of_estimates():
+    """Eq. estiTSM's standard error, var(f_HP - f_LP)/N_HP + var(f_LP)/N_LP, against the
+    spread of the estimate over 4000 independent repetitions (correlated HP/LP pairs)."""
+    rng = np.random.default_rng(7)
+    reps, n_hp, n_lp = 4000, 12, 60
+    f_hp = rng.normal(size=(reps, n_hp))
+    f_pair = 0.9 * f_hp + 0.3 * rng.normal(size=(reps, n_hp))   # the LP map: correlated with HP
+    f_lp = 0.9 * rng.normal(size=(reps, n_lp)) + 0.3 * rng.normal(size=(reps, n_lp))
+    est = np.array([loops.tsm_estimate(f_hp[i], f_pair[i], f_lp[i]) for i in range(reps)])
+    err = np.array([loops.tsm_error(f_hp[i], f_pair[i], f_lp[i]) for i in range(reps)])
+    # exact: var(f_HP - f_LP) = 0.1^2 + 0.3^2, var(f_LP) = 0.9^2 + 0.3^2
+    exact = np.sqrt((0.01 + 0.09) / n_hp + (0.81 + 0.09) / n_lp)
+    assert abs(est.std(ddof=1) / exact - 1) < 0.05
+    assert abs(np.sqrt(np.mean(err ** 2)) / exact - 1) < 0.05
+    # a dropped 1/N factor or a swapped pair of terms would be far off
+    assert abs(np.sqrt((0.1 / n_lp) + (0.9 / n_hp)) / exact - 1) > 0.3
