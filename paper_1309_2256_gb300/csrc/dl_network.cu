@@ -580,7 +580,9 @@ __global__ void __launch_bounds__(256, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
               : "r"(smem_u32(mbar)), "r"((uint32_t)((chunk - 1) & 1)));
           done = r;
         }
-        if (!done) {
+        // one decision for the whole CTA (threads start polling at different times): if
+        // any thread gave up, every thread leaves the chunk loop before its next barrier
+        if (!__syncthreads_and(done)) {
           ok = false;
           if (tid == 0) atomicExch(err, 1);
           break;
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(256, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
           : "r"(smem_u32(mbar)), "r"((uint32_t)((chunk - 1) & 1)));
       done = r;
     }
-    if (!done) {
+    if (!__syncthreads_and(done)) {  // the same decision in every thread
       ok = false;
       if (tid == 0) atomicExch(err, 1);
     }
@@ -698,6 +700,27 @@ __global__ void __launch_bounds__(256, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
 
 namespace dl {
 
+// Backward launches with more than the default 48 KB of dynamic shared memory: the
+// attribute is set (and checked) before every launch.
+template <int PP, int GG>
+cudaError_t launch_bwdx(int grid, size_t smem, const LatDesc& L, int parity, FieldRef ge, FieldRef go, FieldRef gx,
+                        const void* g32, const float2* W, int ci, int co, int lgin, int lgout, cudaStream_t st) {
+  DL_CUDA_TRY(cudaFuncSetAttribute(nn_bwdx_kernel<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DL_COUNT();
+  nn_bwdx_kernel<PP, GG><<<grid, 256, smem, st>>>(L, parity, ge, go, gx, g32, W, ci, co, lgin, lgout);
+  return cudaGetLastError();
+}
+
+template <int PP, int GG>
+cudaError_t launch_bwdw(int grid, size_t smem, const LatDesc& L, int parity, FieldRef xe, FieldRef xo, FieldRef gp,
+                        const void* g32, int ci, int co, int lgin, int lgout, float2* partial, int ntile,
+                        cudaStream_t st) {
+  DL_CUDA_TRY(cudaFuncSetAttribute(nn_bwdw_kernel<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DL_COUNT();
+  nn_bwdw_kernel<PP, GG><<<grid, 256, smem, st>>>(L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial, ntile);
+  return cudaGetLastError();
+}
+
 #define NN_DISPATCH(P, G, CALL)                                       \
   if (P == P32 && G == 12) { constexpr int PP = P32; constexpr int GG = G32R12; CALL; } \
   else if (P == P32 && G == 8) { constexpr int PP = P32; constexpr int GG = G32R8; CALL; } \
@@ -718,10 +741,7 @@ cudaError_t nn_backward_x(const LatDesc& L, int prec, int grec, int parity, Fiel
   if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
   const int grid = (L.Vh + NS - 1) / NS;
   const size_t smem = (size_t)8 * NS * 18 * 4 + 8 * NS * 4 + (size_t)2 * NS * 16 * 24 * 4;
-  NN_DISPATCH(prec, grec, (cudaFuncSetAttribute(nn_bwdx_kernel<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                           DL_COUNT(),
-                           nn_bwdx_kernel<PP, GG><<<grid, 256, smem, st>>>(L, parity, ge, go, gx, g32, W, ci, co, lgin, lgout)));
-  return cudaGetLastError();
+  NN_DISPATCH(prec, grec, return (launch_bwdx<PP, GG>(grid, smem, L, parity, ge, go, gx, g32, W, ci, co, lgin, lgout, st)));
 }
 
 // partial: nslots x (36 * co * ci) complex, this parity's slots start at `partial`;
@@ -733,10 +753,8 @@ cudaError_t nn_backward_w(const LatDesc& L, int prec, int grec, int parity, Fiel
   const int ntile = (L.Vh + NW - 1) / NW;
   const int grid = slots < ntile ? slots : ntile;
   const size_t smem = (size_t)8 * NW * 18 * 4 + 8 * NW * 4 + (size_t)2 * NW * 9 * 16 * 24 * 4 + (size_t)NW * 16 * 24 * 4;
-  NN_DISPATCH(prec, grec, (cudaFuncSetAttribute(nn_bwdw_kernel<PP, GG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                           DL_COUNT(),
-                           nn_bwdw_kernel<PP, GG><<<grid, 256, smem, st>>>(L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial, ntile)));
-  return cudaGetLastError();
+  NN_DISPATCH(prec, grec,
+              return (launch_bwdw<PP, GG>(grid, smem, L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial, ntile, st)));
 }
 
 cudaError_t nn_wsum(const float2* partial, int nslice, size_t nW, float2* grad, cudaStream_t st) {
@@ -795,12 +813,12 @@ cudaError_t nn_forward_tc(const LatDesc& L, int grec, int parity, FieldRef xe, F
   if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
   const int grid = (L.Vh + TC_M - 1) / TC_M;
   if (grec == 12) {
-    cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R12>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    DL_CUDA_TRY(cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R12>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     DL_COUNT();
     nn_fwd_tc_kernel<G32R12><<<grid, 256, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
                                                           lgin, lgout, err);
   } else if (grec == 8) {
-    cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    DL_CUDA_TRY(cudaFuncSetAttribute(nn_fwd_tc_kernel<G32R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     DL_COUNT();
     nn_fwd_tc_kernel<G32R8><<<grid, 256, TC_SMEM, st>>>(L, parity, xe, xo, y, g32, (const __nv_bfloat16*)Bc, ci, co,
                                                          lgin, lgout, err);
