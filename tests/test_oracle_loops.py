@@ -143,6 +143,19 @@ def test_hpe_exact_terms():
             assert abs(val) < 1e-14
 
 
+def test_hpe_exact_terms_need_extents_of_four():
+    """With an extent of 2 two forward hops along that direction return to the site
+    through two different links, so the brute-force exact part differs from the
+    closed form (and from the unit-field value): the closed form holds for extents >= 4."""
+    dims = (4, 4, 2, 4)
+    links = synth.gauge_links(dims, 0.4, 43)
+    c_rand = loops.hpe_exact_c(links, KAPPA, AMU, (0, 0, 0, 0))
+    b = np.linalg.inv(np.eye(4) + 2j * KAPPA * AMU * lattice.GAMMA5)
+    s = sum((np.eye(4) - g) @ b @ (np.eye(4) + g) + (np.eye(4) + g) @ b @ (np.eye(4) - g) for g in lattice.GAMMA)
+    e = 3 * (b + KAPPA ** 2 * b @ s @ b)
+    assert np.abs(c_rand - e.T).max() > 1e-3
+
+
 def test_gauge_invariance_of_loops():
     dims = (4, 4, 2, 4)
     links = synth.gauge_links(dims, 0.4, 51)
