@@ -184,10 +184,22 @@ dl_status dl_momenta(int p2max, int* count, int* list);
 dl_status dl_contract(dl_ctx* ctx, int est, const void* eta, const void* sol, int n,
                       int dtype, int with_deriv, int p2max, double* out, int accumulate);
 
+/* dl_contract for time-diluted sources (Sec. 2.3, dl_noise_z4_tdil): the local loops
+ * (no derivative) on the time slices t = t0 (mod dt) only, 1 <= dt <= T, 0 <= t0 < dt.
+ * out has dl_contract's layout [n][T][Np][1][4][4]; the other slices are written as zero
+ * (or left unchanged with accumulate), where a source that vanishes off its slices has
+ * loops that vanish too.  The contraction work is proportional to the slices kept.
+ * Needs X <= 256. */
+dl_status dl_contract_slices(dl_ctx* ctx, int est, const void* eta, const void* sol, int n,
+                             int dtype, int p2max, int t0, int dt, double* out, int accumulate);
+
 /* Exact part of the hopping-parameter expansion for local insertions (Eq. HPE:
  * orders 0 and 2; orders 1 and 3 vanish on the diagonal): the per-site 4x4
  * matrix C_ab (colour traced) with Tr_x[X (B - BHB + (BH)^2 B - (BH)^3 B)] =
- * sum_ab X_ab C_ab, written to out16 (host, complex128 [4][4]). */
+ * sum_ab X_ab C_ab, written to out16 (host, complex128 [4][4]).  The second order
+ * is the gauge-independent sum over back-and-forth hops, exact when every extent
+ * is at least 4; DL_ERR_ARG otherwise (on an extent of 2, two forward hops also
+ * return to the site).  dl_tsm_run with hpe = 1 has the same requirement. */
 dl_status dl_hpe_exact(dl_ctx* ctx, int flavour, double* out16);
 
 /* ---- truncated solver method (Sec. 2.2, Eq. estiTSM) --------------------- */
@@ -217,6 +229,16 @@ typedef struct {
                             eta^+ X (BH)^4 (s_HP - s_LP) with (BH)^4 applied in FP32 to the
                             difference taken in high precision (relative error ~1e-7 of the
                             correction, not of the loop); 0: both terms in high precision */
+  int tdil_dt, tdil_t0;  /* time dilution (Sec. 2.3): tdil_dt = 0 uses full noise vectors;
+                            otherwise every source is the noise vector restricted to the time
+                            slices t = tdil_t0 (mod tdil_dt) (1 <= tdil_dt <= T, 0 <= tdil_t0 <
+                            tdil_dt; tdil_dt = T: one slice, smaller: coherent sources), as
+                            dl_noise_z4_tdil makes them, and its loops are contracted on those
+                            slices only (zero elsewhere, contraction work in proportion to
+                            the slices kept); local loops only (with_deriv = 0).  The
+                            estimators are then the standard one (Eq. loopSt) and, with hpe,
+                            the HPE one: the one-end trick sums over every sink time of a
+                            source and does not restrict to its slices */
 } dl_tsm_params;
 
 typedef struct {
@@ -233,7 +255,10 @@ typedef struct {
  *   loops  complex128 [n_est][T][Np][nd][4][4]: Eq. estiTSM per element;
  *   obs_hp, obs_lp_pair  double [n_hp][4], obs_lp double [n_lp][4]: per-noise
  *          scalar observables (sigma loop Re, Im; isoscalar axial loop Re, Im;
- *          zero momentum, summed over t) for error estimates. */
+ *          zero momentum, summed over t) for error estimates.
+ * With time dilution (tdil_dt > 0) the estimators are the standard one and, with
+ * hpe, the HPE one (n_est = 1 + hpe), and the observables are the standard
+ * estimator's i g5 and g_z g5 loops on the kept slices. */
 dl_status dl_tsm_run(dl_ctx* ctx, const dl_tsm_params* params, double* loops,
                      double* obs_hp, double* obs_lp_pair, double* obs_lp, dl_tsm_info* info);
 
@@ -300,6 +325,19 @@ dl_status dl_profile(dl_ctx* ctx, int enable, double* out);
  * launches plus the kernel nodes of every CUDA-graph launch).  Thread-safe. */
 long long dl_kernel_launches(void);
 
+/* Stencil launch statistics of the process since profiling was last switched on
+ * (dl_profile with enable = 1 on any context): out (host) receives
+ * double[4 storages][4 epilogues][2][4] = (launches executed, launches timed, summed
+ * milliseconds of the timed ones, summed site-column items of the timed ones) per
+ * class.  Storages: 0 double-float (DL_F64), 1 FP32, 2 16-bit, 3 IEEE FP64.
+ * Epilogues: 0 plain (R^-1 D, B H), 1 with an auxiliary field (R aux - kappa^2 D,
+ * source preparation, reconstruction, M), 2 the same with |.|^2 sums, 3 fused with
+ * the CG update.  The last index is 1 for the daggered hop.  Launches inside the
+ * solver's CUDA graphs are counted per replay and timed through the samples that
+ * dl_profile describes; every other stencil launch is timed with CUDA events on its
+ * stream.  Waits for those events.  Not thread-safe against concurrent profiling. */
+dl_status dl_profile_stencils(double* out);
+
 /* ---- allocation-free variant ----------------------------------------------- */
 
 /* dl_apply without any device allocation.  The paper has no counterpart: this
@@ -314,9 +352,13 @@ long long dl_kernel_launches(void);
  * that array are rejected with DL_ERR_ARG and a message (the limit is
  * 7 x ceil256(V/2 x npad x site bytes [+ 4-byte scales for DL_F16]) <= 64 MiB,
  * npad = n rounded up to a power of two, site bytes 192 / 96 / 48 for
- * DL_F64 / DL_F32 / DL_F16; e.g. 16^3 x 8 with n = 8 in FP64 fits).
+ * DL_F64 / DL_F32 / DL_F16; e.g. 16^3 x 8 with n = 2 in FP64 needs ~44 MB and
+ * fits, with n = 4 it needs ~88 MB and is rejected).
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  The array
+ * device current; make that first call before any stream capture.  The address
+ * is kept for the life of the process: after a cudaDeviceReset (or anything else
+ * that destroys the device's primary context) it is stale, so do not call this
+ * entry point on that device again in the same process.  The array
  * is shared by every call and keeps the previous call's contents (each call
  * overwrites all of it that it reads), so calls that may overlap on the GPU,
  * from any context or stream, race and must be serialised by the caller. */

@@ -42,7 +42,8 @@ class dl_tsm_params(C.Structure):
     _fields_ = [("n_hp", C.c_int), ("n_lp", C.c_int), ("tol_hp", C.c_double), ("tol_lp", C.c_double),
                 ("prec_hp_lo", C.c_int), ("prec_lp_lo", C.c_int), ("delta_hp", C.c_double), ("block", C.c_int),
                 ("seed", C.c_uint64), ("p2max", C.c_int), ("with_deriv", C.c_int), ("hpe", C.c_int),
-                ("max_iter", C.c_int), ("chunk", C.c_int), ("lp_net", C.c_void_p), ("hp_guess", C.c_int), ("hpe_diff", C.c_int)]
+                ("max_iter", C.c_int), ("chunk", C.c_int), ("lp_net", C.c_void_p), ("hp_guess", C.c_int), ("hpe_diff", C.c_int),
+                ("tdil_dt", C.c_int), ("tdil_t0", C.c_int)]
 
 
 class dl_tsm_info(C.Structure):
@@ -97,8 +98,11 @@ _SIGS = {
     "dl_momenta": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_void_p]),
     "dl_contract": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                               C.c_void_p, C.c_int]),
+    "dl_contract_slices": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_int, C.c_void_p, C.c_int]),
     "dl_hpe_exact": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "dl_kernel_launches": (C.c_longlong, []),
+    "dl_profile_stencils": (C.c_int, [C.c_void_p]),
     "dl_apply_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int]),
     "dl_create_multi": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]),
@@ -244,6 +248,11 @@ def dl_contract(ctx, est, eta, sol, n, dtype, with_deriv, p2max, out, accumulate
                                          int(p2max), _ptr(out), int(accumulate)))
 
 
+def dl_contract_slices(ctx, est, eta, sol, n, dtype, p2max, t0, dt, out, accumulate=0):
+    return _check(ctx, lib().dl_contract_slices(ctx, int(est), _ptr(eta), _ptr(sol), int(n), int(dtype), int(p2max),
+                                                int(t0), int(dt), _ptr(out), int(accumulate)))
+
+
 def dl_hpe_exact(ctx, flavour=1):
     out = np.zeros((4, 4), dtype=np.complex128)
     _check(ctx, lib().dl_hpe_exact(ctx, int(flavour), out.ctypes.data))
@@ -261,6 +270,15 @@ def dl_profile(ctx, enable=-1):
     """Returns float64 [4 stages][3 precisions][3] = (launches sampled, ms, items)."""
     out = np.zeros((4, 3, 3), dtype=np.float64)
     _check(ctx, lib().dl_profile(ctx, int(enable), out.ctypes.data))
+    return out
+
+
+def dl_profile_stencils():
+    """float64 [4 storages][4 epilogues][2 dagger][4] = (launches, timed, ms, items)."""
+    out = np.zeros((4, 4, 2, 4), dtype=np.float64)
+    st = lib().dl_profile_stencils(out.ctypes.data)
+    if st < 0:
+        raise DLError(st, "dl_profile_stencils failed")
     return out
 
 

@@ -326,6 +326,10 @@ cudaError_t cg_iteration(dl_ctx* c, const Batch& B, int lo, int f, const CGField
 // Runs after a solve has finished: it leaves r and y modified, which the next
 // solve re-initialises.
 dl_status sample_stencil(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F) {
+  struct Sampling {  // these launches are extra profiling work: timed, not counted
+    Sampling() { dl::stencil_prof_sampling(true); }
+    ~Sampling() { dl::stencil_prof_sampling(false); }
+  } sampling;
   GaugeSet g{c->g64, c->g32, c->g16, c->gdf};
   cudaEvent_t* ev = c->pev;
   CK(cudaEventRecord(ev[0], c->st));
@@ -415,9 +419,11 @@ dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F,
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   const long long before = g_launches.load();
   CK(cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  dl::stencil_capture_begin();
   cudaError_t e = cg_iteration(c, B, lo, f, F, tol2, delta);
   if (e == cudaSuccess)
     e = dl::cg_cond(ncols_of(B), c->active, c->flags, c->loopctr, c->loopctr + 1, c->waitc, h, nullptr, c->st);
+  const dl::StencilTally tally = dl::stencil_capture_end();
   cudaGraph_t captured;
   cudaError_t e2 = cudaStreamEndCapture(c->st, &captured);
   if (e != cudaSuccess) {
@@ -434,7 +440,7 @@ dl_status get_graph(dl_ctx* c, const Batch& B, int lo, int f, const CGFields& F,
     cudaGraphExecDestroy(c->graphs.front().exec);
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back(GraphEntry{key, exec, nodes});
+  c->graphs.push_back(GraphEntry{key, exec, nodes, tally});
   *out = &c->graphs.back();
   return DL_OK;
 }
@@ -523,6 +529,7 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
       CK(cudaMemcpyAsync(&ran, c->loopctr, sizeof(int), cudaMemcpyDeviceToHost, c->st));
       if ((s = download_state(c, n, h)) != DL_OK) return s;
       g_launches.fetch_add(body_kernels * ran);
+      dl::stencil_tally_add(ge->tally, ran);
     } else {
       // the same body and loop condition launched from the host (profilers cannot
       // see kernel nodes inside conditional graphs); one readback per iteration
@@ -756,8 +763,9 @@ int mom_extent(int p2max) {
 // segment's offsets.
 dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int with_deriv, int p2max, Field* s_e,
                             Field* s_o, Field* eta_e, Field* eta_o, double pre_re, double pre_im, double2* out,
-                            int accumulate) {
+                            int accumulate, Slices S = Slices{0, 1, 0}) {
   const LatDesc& L = B.lat[0];
+  if (S.ns == 0) S = all_slices(L.T);
   dl_status s;
   if ((s = ensure_momenta(c, p2max)) != DL_OK) return s;
   const int m = mom_extent(p2max);
@@ -768,9 +776,9 @@ dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int w
   const size_t V = 2ull * L.Vh;
   const bool fused = L.X <= 256;  // one CTA per (row, column group) holds X * cw <= 256 sites
   const size_t nW = fused ? 0 : (size_t)ncomp * V * npad;
-  const size_t nG1 = (size_t)ncomp * L.T * L.Z * L.Y * NX * npad;
-  const size_t nG2 = (size_t)ncomp * L.T * L.Z * NY * NX * npad;
-  const size_t nG3 = (size_t)ncomp * L.T * NZ * NY * NX * npad;
+  const size_t nG1 = (size_t)ncomp * S.ns * L.Z * L.Y * NX * npad;
+  const size_t nG2 = (size_t)ncomp * S.ns * L.Z * NY * NX * npad;
+  const size_t nG3 = (size_t)ncomp * S.ns * NZ * NY * NX * npad;
   const size_t nph = 17 * 256 + 64;  // phase tables (x: up to 17 momenta x 256 sites of 16-byte pairs)
   if ((s = ensure_scratch(c, sizeof(double2) * (nW + nG1 + nG2 + nG3 + nph))) != DL_OK) return s;
   double2* W = (double2*)c->scratch;
@@ -783,16 +791,18 @@ dl_status contract_internal(dl_ctx* c, const Batch& B, int prec, int mode, int w
   const int fp32 = !fused ? 0 : (prec == P32 ? 1 : (prec == PDF ? 2 : 0));
   if (fused) {
     CK(dl::contract_x(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
-                      eta_o ? eta_o->ref() : NOF, prec == PDF ? c->gdf : c->g64, c->g32, c->rec32, mx, ph, G1,
+                      eta_o ? eta_o->ref() : NOF, prec == PDF ? c->gdf : c->g64, c->g32, c->rec32, mx, ph, G1, S,
                       c->st));
   } else {
+    if (S.ns != L.T) return fail(c, DL_ERR_ARG, "slice-restricted contractions need X <= 256");
     CK(dl::contract_sites(B, prec, mode, with_deriv, s_e->ref(), s_o->ref(), eta_e ? eta_e->ref() : NOF,
                           eta_o ? eta_o->ref() : NOF, c->g64, W, c->st));
     CK(dl::dft_pass(W, G1, (long long)ncomp * L.T * L.Z * L.Y, L.X, npad, mx, ph, fp32, c->st));
   }
-  CK(dl::dft_pass(G1, G2, (long long)ncomp * L.T * L.Z, L.Y, (long long)NX * npad, my, ph, fp32, c->st));
-  CK(dl::dft_pass(G2, G3, (long long)ncomp * L.T, L.Z, (long long)NY * NX * npad, mz, ph, fp32, c->st));
-  CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, fp32, pre_re, pre_im, out, accumulate, c->st));
+  CK(dl::dft_pass(G1, G2, (long long)ncomp * S.ns * L.Z, L.Y, (long long)NX * npad, my, ph, fp32, c->st));
+  CK(dl::dft_pass(G2, G3, (long long)ncomp * S.ns, L.Z, (long long)NY * NX * npad, mz, ph, fp32, c->st));
+  CK(dl::contract_finalize(B, with_deriv, c->np, c->mom, mx, my, mz, G3, fp32, pre_re, pre_im, out, accumulate, S,
+                           c->st));
   return DL_OK;
 }
 
@@ -1214,6 +1224,7 @@ dl_status dl_profile(dl_ctx* c, int enable, double* out) try {
   }
   if (enable >= 0) {
     if ((enable != 0) != (c->profiling != 0)) invalidate_graphs(c);
+    dl::stencil_prof_enable(enable != 0);
     c->profiling = enable != 0;
     c->prof_pending[0] = c->prof_pending[1] = c->prof_pending[2] = c->profiling;
     memset(c->prof_ms, 0, sizeof(c->prof_ms));
@@ -1224,6 +1235,11 @@ dl_status dl_profile(dl_ctx* c, int enable, double* out) try {
 } DL_CATCH(c)
 
 long long dl_kernel_launches(void) { return g_launches.load(); }
+
+dl_status dl_profile_stencils(double* out) try {
+  if (!out) return DL_ERR_ARG;
+  return dl::stencil_prof_read(out) == cudaSuccess ? DL_OK : DL_ERR_CUDA;
+} DL_CATCH(nullptr)
 
 dl_status dl_momenta(int p2max, int* count, int* list) try {
   if (!count || p2max < 0 || p2max > 64) return DL_ERR_ARG;
@@ -1244,8 +1260,10 @@ dl_status dl_momenta(int p2max, int* count, int* list) try {
   return DL_OK;
 } DL_CATCH(nullptr)
 
-dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int with_deriv, int p2max,
-                      double* out, int accumulate) try {
+// dl_contract and dl_contract_slices: pack the natural fields, apply (BH)^4 for the HPE
+// estimator, contract on the slices S
+static dl_status contract_api(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int with_deriv,
+                              int p2max, double* out, int accumulate, Slices S) {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
   if (!sol || !out || n < 1 || n > DL_MAX_RHS || est < 0 || est > 3 || p2max < 0 || p2max > 64 ||
@@ -1281,13 +1299,41 @@ dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int 
     pre_re = 2.0;
   }
   if ((s = contract_internal(c, B, prec, est, with_deriv, p2max, we, wo, ee, eo, pre_re, pre_im, (double2*)out,
-                             accumulate)) != DL_OK)
+                             accumulate, S)) != DL_OK)
     return s;
   return leave(c);
+}
+
+dl_status dl_contract(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int with_deriv, int p2max,
+                      double* out, int accumulate) try {
+  if (!c) return DL_ERR_ARG;
+  return contract_api(c, est, eta, sol, n, dtype, with_deriv, p2max, out, accumulate, all_slices(c->dims[3]));
 } DL_CATCH(c)
+
+dl_status dl_contract_slices(dl_ctx* c, int est, const void* eta, const void* sol, int n, int dtype, int p2max, int t0,
+                             int dt, double* out, int accumulate) try {
+  if (!c) return DL_ERR_ARG;
+  const int T = c->dims[3];
+  if (dt < 1 || dt > T || t0 < 0 || t0 >= dt)
+    return fail(c, DL_ERR_ARG, "dl_contract_slices: need 1 <= dt <= T and 0 <= t0 < dt");
+  return contract_api(c, est, eta, sol, n, dtype, 0, p2max, out, accumulate, Slices{t0, dt, (T - 1 - t0) / dt + 1});
+} DL_CATCH(c)
+
+// The closed form of the exact HPE orders counts only the back-and-forth paths of two
+// hops; on a lattice with an extent of 2 two forward hops also return to the site
+// (through two different links), so the form is exact only for extents >= 4.
+static bool hpe_exact_valid(const dl_ctx* c) {
+  for (const auto& L : c->lats)
+    for (int k = 0; k < 4; ++k)
+      if (L.dims[k] < 4) return false;
+  return true;
+}
 
 dl_status dl_hpe_exact(dl_ctx* c, int flavour, double* out16) try {
   if (!c || !out16 || (flavour != 1 && flavour != -1)) return DL_ERR_ARG;
+  if (!hpe_exact_valid(c))
+    return fail(c, DL_ERR_ARG, "dl_hpe_exact: every lattice extent must be at least 4 (with an extent of 2, two "
+                               "forward hops return to the site and the closed form misses those paths)");
   dl_status s;
   if ((s = enter(c)) != DL_OK) return s;
   CK(dl::hpe_exact(c->kappa, c->amu, flavour, c->misc, c->st));
@@ -1306,13 +1352,33 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
       prm->delta_hp < 0.0 || prm->delta_hp >= 1.0)
     return fail(c, DL_ERR_ARG, "dl_tsm_run: bad parameters");
   if (prm->hpe && prm->with_deriv) return fail(c, DL_ERR_ARG, "dl_tsm_run: the HPE estimator is local only");
+  if (prm->hpe && !hpe_exact_valid(c))
+    return fail(c, DL_ERR_ARG, "dl_tsm_run: the HPE estimator needs every lattice extent >= 4 (its exact orders)");
+  // time-diluted sources (Sec. 2.3): noise on the slices t = t0 (mod dt) only, contracted there only
+  Slices S = all_slices(c->dims[3]);
+  if (prm->tdil_dt != 0) {
+    const int T = c->dims[3];
+    if (prm->tdil_dt < 1 || prm->tdil_dt > T || prm->tdil_t0 < 0 || prm->tdil_t0 >= prm->tdil_dt)
+      return fail(c, DL_ERR_ARG, "dl_tsm_run: time dilution needs 1 <= tdil_dt <= T and 0 <= tdil_t0 < tdil_dt");
+    if (prm->with_deriv)
+      return fail(c, DL_ERR_ARG, "dl_tsm_run: time-diluted sources are contracted into local loops only");
+    S = Slices{prm->tdil_t0, prm->tdil_dt, (T - 1 - prm->tdil_t0) / prm->tdil_dt + 1};
+  }
   if ((s = enter(c)) != DL_OK) return s;
   auto t_all = std::chrono::steady_clock::now();
   if (c->profiling) c->prof_pending[0] = c->prof_pending[1] = c->prof_pending[2] = 1;
   if ((s = ensure_momenta(c, prm->p2max)) != DL_OK) return s;
   const int np = c->np, nd = prm->with_deriv ? 5 : 1, T = c->dims[3];
-  const int n_est = prm->hpe ? 3 : 2;
-  const int est_mode[3] = {DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE};
+  // estimators: one-end, generalised one-end (and HPE); for time-diluted sources the
+  // standard estimator (and HPE): the one-end trick sums over every sink time of one
+  // source and does not restrict to the source's slices
+  const bool tdil = prm->tdil_dt != 0;
+  const int n_est = tdil ? (prm->hpe ? 2 : 1) : (prm->hpe ? 3 : 2);
+  int est_mode[3] = {DL_EST_ONE_END, DL_EST_GEN, DL_EST_HPE};
+  if (tdil) {
+    est_mode[0] = DL_EST_STANDARD;
+    est_mode[1] = DL_EST_HPE;
+  }
   const long long per = (long long)T * np * nd * 16;
   const int blk = prm->block;
   double2 *acc_d, *acc_l, *bl, *bh, *res;
@@ -1373,8 +1439,8 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
         (s2 = ensure_field(c, std::string("ts_xe") + tag, hi, B, &xe)) ||
         (s2 = ensure_field(c, std::string("ts_po") + tag, hi, B, &po)))
       return s2;
-    CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, first, 0, c->st));
-    CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, first, 0, c->st));
+    CK(dl::noise_z4(B, hi, 0, ee->ref(), prm->seed, first, 0, c->st, S));
+    CK(dl::noise_z4(B, hi, 1, eo->ref(), prm->seed, first, 0, c->st, S));
     bool guess = false;
     if (hp && prm->hp_guess) {  // start from the LP solution of the same noise (same block, FP32 field)
       Field* lp_xe;
@@ -1405,27 +1471,30 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
         CK(dl::copy(B, P32, hi, e3->ref(), ee->ref(), nullptr, c->st));
         CK(dl::copy(B, P32, hi, o3->ref(), eo->ref(), nullptr, c->st));
         if ((s2 = bh_power(c, B, P32, 1, 4, de, dd, &we, &wo)) != DL_OK) return s2;
-        if ((s2 = contract_internal(c, B, P32, DL_EST_HPE, 0, prm->p2max, we, wo, e3, o3, 1.0, 0.0, o, 0)) != DL_OK)
+        if ((s2 = contract_internal(c, B, P32, DL_EST_HPE, 0, prm->p2max, we, wo, e3, o3, 1.0, 0.0, o, 0, S)) != DL_OK)
           return s2;
       } else if (est_mode[e] == DL_EST_HPE) {
         Field *we, *wo;
         if ((s2 = bh_power(c, B, hi, 1, 4, xe, po, &we, &wo)) != DL_OK) return s2;
-        if ((s2 = contract_internal(c, B, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0)) != DL_OK) return s2;
-        CK(dl::add_exact_p0(B, np, nd, ip0, c->misc, Ls, o, c->st));
+        if ((s2 = contract_internal(c, B, hi, DL_EST_HPE, 0, prm->p2max, we, wo, ee, eo, 1.0, 0.0, o, 0, S)) != DL_OK)
+          return s2;
+        CK(dl::add_exact_p0(B, np, nd, ip0, c->misc, Ls, o, S, c->st));
       } else {
-        double pr = 1.0, pi = 0.0;
+        double pr = 1.0, pi = 0.0;  // the estimator's factor (Eqs. loopSt, loopVv, loopStD)
         if (est_mode[e] == DL_EST_ONE_END) {
           pr = 0.0;
           pi = -4.0 * c->kappa * c->amu;
-        } else {
+        } else if (est_mode[e] == DL_EST_GEN) {
           pr = 2.0;
         }
-        if ((s2 = contract_internal(c, B, hi, est_mode[e], prm->with_deriv, prm->p2max, xe, po, ee, eo, pr, pi, o, 0)) !=
+        if ((s2 = contract_internal(c, B, hi, est_mode[e], prm->with_deriv, prm->p2max, xe, po, ee, eo, pr, pi, o, 0, S)) !=
             DL_OK)
           return s2;
       }
     }
-    CK(dl::observables(out, out + (size_t)per * blk, n, T, np, nd, ip0, obs, c->st));
+    // per-noise observables: i g5 and g_z g5 loops (one-end and generalised; both from
+    // the standard estimator for time-diluted sources)
+    CK(dl::observables(out, tdil ? out : out + (size_t)per * blk, n, T, np, nd, ip0, obs, c->st));
     CK(cudaStreamSynchronize(c->st));
     t_ct += std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count();
     return rs;

@@ -206,7 +206,7 @@ template <int P, int MODE, bool DERIV, typename R, int G, int MXT>
 __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                                                            FieldRef eta_o, const void* __restrict__ gbase, int mx,
                                                            int cwlog, const RPair<R>* __restrict__ phx,
-                                                           RPair<R>* __restrict__ G1) {
+                                                           RPair<R>* __restrict__ G1, Slices S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const LatDesc& L = B.lat[0];
   const int lg = L.lognpad, npad = 1 << lg;
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
   cr* cs = (cr*)smem_raw;                        // [16][X][cw] site components
   cr* pht = cs + 16 * L.X * cw;                  // [NX][X] phases
   cr* part = pht + NX * L.X;                     // [2 halves][16][NX][cw] partial DFT sums
-  const int row = blockIdx.x;                    // (t * Z + z) * Y + y
-  const int y = row % L.Y, z = (row / L.Y) % L.Z, t = row / (L.Y * L.Z);
+  const int row = blockIdx.x;                    // (k * Z + z) * Y + y for slice t = t0 + k dt
+  const int y = row % L.Y, z = (row / L.Y) % L.Z, t = S.t0 + S.dt * (row / (L.Y * L.Z));
   const int x = threadIdx.x >> cwlog, cl = threadIdx.x & (cw - 1);
   const int col = blockIdx.y * cw + cl;
   for (int e = threadIdx.x; e < NX * L.X; e += blockDim.x) pht[e] = phx[e];
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
   const bool live = col < L.ncol;
   R xi[24], phi[24];
   if (live) make_pair<P, MODE, R>(p ? s_o : s_e, p ? eta_o : eta_e, L, nitems, ((long long)(lex >> 1) << lg) + col, xi, phi);
-  const long long nrows = (long long)L.T * L.Z * L.Y;
+  const long long nrows = (long long)S.ns * L.Z * L.Y;
   const int nd = DERIV ? 5 : 1;
   for (int d = 0; d < nd; ++d) {
     R cre[16], cim[16];
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) dft_kernel(const RPair<R>* __restrict__ i
 template <typename R>
 __global__ void finalize_kernel(LatDesc L, int npad, int nd, int np, const int* __restrict__ mom, int mx, int my, int mz,
                                 const RPair<R>* __restrict__ G3,
-                                double pre_re, double pre_im, double2* out, int accumulate) {
+                                double pre_re, double pre_im, double2* out, int accumulate, Slices S) {
   const long long tot = (long long)L.ncol * L.T * np * nd * 16;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= tot) return;
@@ -427,8 +427,11 @@ __global__ void finalize_kernel(LatDesc L, int npad, int nd, int np, const int* 
   int nx = mom[3 * ip], ny = mom[3 * ip + 1], nz = mom[3 * ip + 2];
   const int NX = 2 * mx + 1, NY = 2 * my + 1, NZ = 2 * mz + 1;
   const long long cube = (long long)NZ * NY * NX * npad;
+  // G3 holds the covered slices only (index k of t = t0 + k dt); other slices are zero
   auto g = [&](int comp, int tt) -> double2 {
-    long long o = ((long long)comp * L.T + tt) * cube + (((long long)(nz + mz) * NY + (ny + my)) * NX + (nx + mx)) * npad + col;
+    const int k = slice_index(S, tt);
+    if (k < 0) return make_double2(0.0, 0.0);
+    long long o = ((long long)comp * S.ns + k) * cube + (((long long)(nz + mz) * NY + (ny + my)) * NX + (nx + mx)) * npad + col;
     return make_double2((double)G3[o].x, (double)G3[o].y);
   };
   double2 v;
@@ -526,7 +529,7 @@ __global__ void hpe_exact_kernel(double kappa, double amu, int flavour, double2*
 }
 
 __global__ void add_exact_kernel(LatDesc L, int np, int nd, int ip0, const double2* __restrict__ ex, double scale,
-                                 double2* out) {
+                                 double2* out, Slices S) {
   long long tot = (long long)L.ncol * L.T * 16;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= tot) return;
@@ -534,6 +537,7 @@ __global__ void add_exact_kernel(LatDesc L, int np, int nd, int ip0, const doubl
   long long r = idx / 16;
   int t = (int)(r % L.T);
   int col = (int)(r / L.T);
+  if (slice_index(S, t) < 0) return;  // the source is zero on this slice: no exact part either
   long long o = ((((long long)col * L.T + t) * np + ip0) * nd + 0) * 16 + ab;
   out[o].x += scale * ex[ab].x;
   out[o].y += scale * ex[ab].y;
@@ -641,17 +645,18 @@ cudaError_t contract_sites(const Batch& B, int prec, int mode, int with_deriv, F
 
 template <int PR, int MD, bool DV, typename R, int G, int MXT>
 cudaError_t launch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx, FieldRef s_e, FieldRef s_o,
-                      FieldRef eta_e, FieldRef eta_o, const void* gb, double2* phx, double2* G1, cudaStream_t st) {
+                      FieldRef eta_e, FieldRef eta_o, const void* gb, double2* phx, double2* G1, Slices S,
+                      cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   const int NX = 2 * mx + 1;
   const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 32 * NX * (1 << cwlog)) * 2 * sizeof(R);
   if (smem > 200000) return cudaErrorInvalidValue;
   DL_COUNT();
   phase_table_kernel<R><<<(NX * L.X + 255) / 256, 256, 0, st>>>(L.X, mx, (RPair<R>*)phx);
-  cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G, MXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+  DL_CUDA_TRY(cudaFuncSetAttribute(contract_x_kernel<PR, MD, DV, R, G, MXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000));
   DL_COUNT();
   contract_x_kernel<PR, MD, DV, R, G, MXT><<<grid, threads, smem, st>>>(B, s_e, s_o, eta_e, eta_o, gb, mx, cwlog,
-                                                                         (const RPair<R>*)phx, (RPair<R>*)G1);
+                                                                         (const RPair<R>*)phx, (RPair<R>*)G1, S);
   return cudaGetLastError();
 }
 
@@ -660,34 +665,34 @@ cudaError_t launch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx,
 template <int PR, int MD, bool DV>
 cudaError_t dispatch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx, FieldRef s_e, FieldRef s_o,
                         FieldRef eta_e, FieldRef eta_o, const void* g64, const void* g32, int rec32, double2* phx,
-                        double2* G1, cudaStream_t st) {
+                        double2* G1, Slices S, cudaStream_t st) {
 #define ARGS B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o
   if constexpr (PR == P64) {
-    return launch_cx<PR, MD, DV, double, G64R18, -1>(ARGS, g64, phx, G1, st);
+    return launch_cx<PR, MD, DV, double, G64R18, -1>(ARGS, g64, phx, G1, S, st);
   } else if constexpr (PR == PDF) {
-    return launch_cx<PR, MD, DV, dfloat, GDF18, -1>(ARGS, g64, phx, G1, st);
+    return launch_cx<PR, MD, DV, dfloat, GDF18, -1>(ARGS, g64, phx, G1, S, st);
   } else {
     if constexpr (!DV) {
       if (rec32 == 12) {
         switch (mx) {
-          case 0: return launch_cx<PR, MD, DV, float, G32R12, 0>(ARGS, g32, phx, G1, st);
-          case 1: return launch_cx<PR, MD, DV, float, G32R12, 1>(ARGS, g32, phx, G1, st);
-          case 2: return launch_cx<PR, MD, DV, float, G32R12, 2>(ARGS, g32, phx, G1, st);
-          case 3: return launch_cx<PR, MD, DV, float, G32R12, 3>(ARGS, g32, phx, G1, st);
+          case 0: return launch_cx<PR, MD, DV, float, G32R12, 0>(ARGS, g32, phx, G1, S, st);
+          case 1: return launch_cx<PR, MD, DV, float, G32R12, 1>(ARGS, g32, phx, G1, S, st);
+          case 2: return launch_cx<PR, MD, DV, float, G32R12, 2>(ARGS, g32, phx, G1, S, st);
+          case 3: return launch_cx<PR, MD, DV, float, G32R12, 3>(ARGS, g32, phx, G1, S, st);
           default: break;
         }
       } else {
         switch (mx) {
-          case 0: return launch_cx<PR, MD, DV, float, G32R8, 0>(ARGS, g32, phx, G1, st);
-          case 1: return launch_cx<PR, MD, DV, float, G32R8, 1>(ARGS, g32, phx, G1, st);
-          case 2: return launch_cx<PR, MD, DV, float, G32R8, 2>(ARGS, g32, phx, G1, st);
-          case 3: return launch_cx<PR, MD, DV, float, G32R8, 3>(ARGS, g32, phx, G1, st);
+          case 0: return launch_cx<PR, MD, DV, float, G32R8, 0>(ARGS, g32, phx, G1, S, st);
+          case 1: return launch_cx<PR, MD, DV, float, G32R8, 1>(ARGS, g32, phx, G1, S, st);
+          case 2: return launch_cx<PR, MD, DV, float, G32R8, 2>(ARGS, g32, phx, G1, S, st);
+          case 3: return launch_cx<PR, MD, DV, float, G32R8, 3>(ARGS, g32, phx, G1, S, st);
           default: break;
         }
       }
     }
-    if (rec32 == 12) return launch_cx<PR, MD, DV, float, G32R12, -1>(ARGS, g32, phx, G1, st);
-    return launch_cx<PR, MD, DV, float, G32R8, -1>(ARGS, g32, phx, G1, st);
+    if (rec32 == 12) return launch_cx<PR, MD, DV, float, G32R12, -1>(ARGS, g32, phx, G1, S, st);
+    return launch_cx<PR, MD, DV, float, G32R8, -1>(ARGS, g32, phx, G1, S, st);
   }
 #undef ARGS
 }
@@ -698,7 +703,7 @@ namespace dl {
 
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                        FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* phx, double2* G1,
-                       cudaStream_t st) {
+                       Slices S, cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   const int npad = 1 << L.lognpad;
   int cwlog = L.lognpad;
@@ -707,13 +712,15 @@ cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, Field
   if (threads > 256 || threads < 1) return cudaErrorInvalidValue;
   if (prec == P32 && rec32 != 12 && rec32 != 8) return cudaErrorInvalidValue;
   if (2 * mx + 1 > DL_NXMAX) return cudaErrorInvalidValue;
-  const dim3 grid(L.T * L.Z * L.Y, npad >> cwlog);
+  if (S.ns < 1 || S.dt < 1 || S.t0 < 0 || S.t0 + S.dt * (S.ns - 1) >= L.T) return cudaErrorInvalidValue;
+  if (with_deriv && S.ns != L.T) return cudaErrorInvalidValue;  // the derivative reaches t - 1 and t + 1
+  const dim3 grid(S.ns * L.Z * L.Y, npad >> cwlog);
 #define CX(PR, MD)                                                                                                  \
   if (prec == PR && mode == MD)                                                                                    \
     return with_deriv ? dispatch_cx<PR, MD, true>(B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o, g64, g32,   \
-                                                  rec32, phx, G1, st)                                              \
+                                                  rec32, phx, G1, S, st)                                           \
                       : dispatch_cx<PR, MD, false>(B, grid, threads, cwlog, mx, s_e, s_o, eta_e, eta_o, g64, g32,  \
-                                                   rec32, phx, G1, st);
+                                                   rec32, phx, G1, S, st);
   CX(P64, 0) CX(P64, 1) CX(P64, 2) CX(P64, 3)
   CX(P32, 0) CX(P32, 1) CX(P32, 2) CX(P32, 3)
   CX(PDF, 0) CX(PDF, 1) CX(PDF, 2) CX(PDF, 3)
@@ -734,16 +741,16 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
     return cudaErrorInvalidValue;  // extents up to ~190 (FP64) / ~380 (FP32) sites
   if (fp32 == 2) {  // double-float pairs
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(dfloat);
-    cudaFuncSetAttribute(dft_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    DL_CUDA_TRY(cudaFuncSetAttribute(dft_kernel<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000));
     dft_kernel<dfloat><<<(int)g, 256, smem, st>>>((const RPair<dfloat>*)in, (RPair<dfloat>*)out, nb, len, stride, m,
                                                  phase);
   } else if (fp32 == 1) {  // in and out hold float pairs
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(float);
-    cudaFuncSetAttribute(dft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    DL_CUDA_TRY(cudaFuncSetAttribute(dft_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000));
     dft_kernel<float><<<(int)g, 256, smem, st>>>((const RPair<float>*)in, (RPair<float>*)out, nb, len, stride, m, phase);
   } else {
     const size_t smem = (size_t)(len * DL_DFT_TILE + len) * 2 * sizeof(double);
-    cudaFuncSetAttribute(dft_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000);
+    DL_CUDA_TRY(cudaFuncSetAttribute(dft_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200000));
     dft_kernel<double><<<(int)g, 256, smem, st>>>((const RPair<double>*)in, (RPair<double>*)out, nb, len, stride, m,
                                                  phase);
   }
@@ -752,7 +759,7 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
 
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
                               const double2* G3, int fp32, double pre_re, double pre_im, double2* out, int accumulate,
-                              cudaStream_t st) {
+                              Slices S, cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   int nd = with_deriv ? 5 : 1;
   long long tot = (long long)L.ncol * L.T * np * nd * 16;
@@ -761,15 +768,15 @@ cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int*
   if (fp32 == 2)
     finalize_kernel<dfloat><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
                                                                      (const RPair<dfloat>*)G3, pre_re, pre_im, out,
-                                                                     accumulate);
+                                                                     accumulate, S);
   else if (fp32 == 1)
     finalize_kernel<float><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
                                                                     (const RPair<float>*)G3, pre_re, pre_im, out,
-                                                                    accumulate);
+                                                                    accumulate, S);
   else
     finalize_kernel<double><<<(int)((tot + 255) / 256), 256, 0, st>>>(L, 1 << L.lognpad, nd, np, mom_dev, mx, my, mz,
                                                                      (const RPair<double>*)G3, pre_re, pre_im, out,
-                                                                     accumulate);
+                                                                     accumulate, S);
   return cudaGetLastError();
 }
 
@@ -780,11 +787,11 @@ cudaError_t hpe_exact(double kappa, double amu, int flavour, double2* out16, cud
 }
 
 cudaError_t add_exact_p0(const Batch& B, int np, int nd, int ip0, const double2* exact16, double scale, double2* out,
-                         cudaStream_t st) {
+                         Slices S, cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   long long tot = (long long)L.ncol * L.T * 16;
   DL_COUNT();
-  add_exact_kernel<<<(int)((tot + 255) / 256), 256, 0, st>>>(L, np, nd, ip0, exact16, scale, out);
+  add_exact_kernel<<<(int)((tot + 255) / 256), 256, 0, st>>>(L, np, nd, ip0, exact16, scale, out, S);
   return cudaGetLastError();
 }
 

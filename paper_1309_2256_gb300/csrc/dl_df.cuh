@@ -84,3 +84,49 @@ DF_HD dfloat& operator*=(dfloat& a, const dfloat& b) {
   a = a * b;
   return a;
 }
+
+// Lazy accumulation (sums of many terms, e.g. the stencil's SU(3) products and its
+// sum over hops): the running sum is kept as an unnormalised pair (hi, lo) whose hi
+// part is updated by an exact two-sum and whose lo part collects the two-sum errors
+// and the terms' own low parts in FP32; df_normalize makes it a dfloat again.  Each
+// FP32 addition into lo errs by at most 2^-24 |lo| ~ 2^-48 of the sum's scale, so the
+// result keeps the double-float accuracy of the terms (absolute error ~2^-47 times
+// the sum of their magnitudes) at about half the operations of repeated dfloat adds.
+DF_HD void df_acc(dfloat& s, const dfloat& t) {  // s += t
+  float h, e;
+  df_two_sum(s.hi, t.hi, h, e);
+  s.lo = s.lo + (t.lo + e);
+  s.hi = h;
+}
+// s += a * b, the product's leading part exact (FMA) and both cross terms added to lo
+// (a.lo * b.lo, below 2^-48 of the product, is dropped)
+DF_HD void df_acc_mul(dfloat& s, const dfloat& a, const dfloat& b) {
+  const float p = a.hi * b.hi;
+  float c = df_fma(a.hi, b.hi, -p);
+  c = df_fma(a.hi, b.lo, c);
+  c = df_fma(a.lo, b.hi, c);
+  float h, e;
+  df_two_sum(s.hi, p, h, e);
+  s.lo = s.lo + (c + e);
+  s.hi = h;
+}
+// the first term of a lazy sum: s = a * b
+DF_HD dfloat df_mul_lazy(const dfloat& a, const dfloat& b) {
+  const float p = a.hi * b.hi;
+  float c = df_fma(a.hi, b.hi, -p);
+  c = df_fma(a.hi, b.lo, c);
+  c = df_fma(a.lo, b.hi, c);
+  return dfloat(p, c);
+}
+// a + b and a - b as unnormalised pairs (exact two-sum of the hi parts)
+DF_HD dfloat df_add_lazy(const dfloat& a, const dfloat& b) {
+  float h, e;
+  df_two_sum(a.hi, b.hi, h, e);
+  return dfloat(h, (a.lo + b.lo) + e);
+}
+// (a full two-sum: after cancellation in the hi parts |lo| may exceed |hi|)
+DF_HD dfloat df_normalize(const dfloat& s) {
+  float h, e;
+  df_two_sum(s.hi, s.lo, h, e);
+  return dfloat(h, e);
+}

@@ -23,6 +23,7 @@ struct GraphEntry {
   std::string key;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;  // kernel nodes in the graph
+  dl::StencilTally tally;  // stencil launches of one replay of the body, by class
 };
 
 inline int ilog2ceil(int n) {

@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 #define DL_MAX_LAT 16
 #define DL_MAXC 32  // max columns (right-hand sides) per lattice segment
@@ -496,6 +497,95 @@ __device__ __forceinline__ void hop_term(R acc[24], const R v[24], const R u[18]
   }
 }
 
+// The same hop in double-float with lazy sums (dl_df.cuh): acc holds unnormalised
+// (hi, lo) pairs during the eight hops and is normalised once before the epilogue.
+// The projector sign s and the factor w are +-1 here (double-float storage has no
+// scale; the boundary sign is folded into the staged link).
+template <bool DAGU, int mu>
+__device__ __forceinline__ void hop_term_df(dfloat acc[24], const dfloat v[24], const dfloat u[18], dfloat s, dfloat w) {
+  const bool sp_ = s.hi > 0.f, wp = w.hi > 0.f;
+  auto sg = [](bool pos, const dfloat& x) { return pos ? x : -x; };
+  dfloat hr[2][3], hi[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const dfloat u0r = v[2 * c], u0i = v[2 * c + 1], u1r = v[6 + 2 * c], u1i = v[7 + 2 * c];
+    const dfloat d2r = v[12 + 2 * c], d2i = v[13 + 2 * c], d3r = v[18 + 2 * c], d3i = v[19 + 2 * c];
+    if (mu == 0) {         // (G d)_0 = -i d3, (G d)_1 = -i d2
+      hr[0][c] = df_add_lazy(u0r, sg(sp_, d3i)); hi[0][c] = df_add_lazy(u0i, sg(!sp_, d3r));
+      hr[1][c] = df_add_lazy(u1r, sg(sp_, d2i)); hi[1][c] = df_add_lazy(u1i, sg(!sp_, d2r));
+    } else if (mu == 1) {  // (G d)_0 = -d3, (G d)_1 = d2
+      hr[0][c] = df_add_lazy(u0r, sg(!sp_, d3r)); hi[0][c] = df_add_lazy(u0i, sg(!sp_, d3i));
+      hr[1][c] = df_add_lazy(u1r, sg(sp_, d2r)); hi[1][c] = df_add_lazy(u1i, sg(sp_, d2i));
+    } else if (mu == 2) {  // (G d)_0 = -i d2, (G d)_1 = i d3
+      hr[0][c] = df_add_lazy(u0r, sg(sp_, d2i)); hi[0][c] = df_add_lazy(u0i, sg(!sp_, d2r));
+      hr[1][c] = df_add_lazy(u1r, sg(!sp_, d3i)); hi[1][c] = df_add_lazy(u1i, sg(sp_, d3r));
+    } else {               // G = 1
+      hr[0][c] = df_add_lazy(u0r, sg(sp_, d2r)); hi[0][c] = df_add_lazy(u0i, sg(sp_, d2i));
+      hr[1][c] = df_add_lazy(u1r, sg(sp_, d3r)); hi[1][c] = df_add_lazy(u1i, sg(sp_, d3i));
+    }
+  }
+  const bool sw = sp_ == wp;  // sign of s w
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      // chi = U' h for output colour a of spin sp; U' = U or U^dagger (conj(U_ba))
+      dfloat cr, ci;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const dfloat ur = DAGU ? u[2 * (3 * b + a)] : u[2 * (3 * a + b)];
+        const dfloat ui = DAGU ? -u[2 * (3 * b + a) + 1] : u[2 * (3 * a + b) + 1];
+        if (b == 0) {
+          cr = df_mul_lazy(ur, hr[sp][b]);
+          ci = df_mul_lazy(ur, hi[sp][b]);
+        } else {
+          df_acc_mul(cr, ur, hr[sp][b]);
+          df_acc_mul(ci, ur, hi[sp][b]);
+        }
+        df_acc_mul(cr, -ui, hi[sp][b]);
+        df_acc_mul(ci, ui, hr[sp][b]);
+      }
+      cr = df_normalize(cr);
+      ci = df_normalize(ci);
+      // acc_up += w chi;  acc_dn += s w G^dagger chi
+      df_acc(acc[6 * sp + 2 * a], sg(wp, cr));
+      df_acc(acc[6 * sp + 2 * a + 1], sg(wp, ci));
+      // G^dagger maps upper spin sp to lower spin: mu 0: (i c1, i c0); 1: (c1, -c0);
+      // 2: (i c0, -i c1); 3: (c0, c1)   [lower spin 2 from c_1 or c_0, lower 3 likewise]
+      int lo_sp;
+      bool neg, imul;
+      if (mu == 0) { lo_sp = sp == 1 ? 2 : 3; neg = false; imul = true; }
+      else if (mu == 1) { lo_sp = sp == 1 ? 2 : 3; neg = sp == 0; imul = false; }
+      else if (mu == 2) { lo_sp = sp == 0 ? 2 : 3; neg = sp == 1; imul = true; }
+      else { lo_sp = sp == 0 ? 2 : 3; neg = false; imul = false; }
+      const bool pos = (sw != neg);  // overall sign of the term
+      dfloat* t = &acc[6 * lo_sp + 2 * a];
+      if (imul) {  // +-i (cr + i ci) = +-(-ci + i cr)
+        df_acc(t[0], sg(!pos, ci));
+        df_acc(t[1], sg(pos, cr));
+      } else {
+        df_acc(t[0], sg(pos, cr));
+        df_acc(t[1], sg(pos, ci));
+      }
+    }
+  }
+}
+
+// The hop of the staged and direct stencils for every arithmetic type.
+template <typename R, bool DAGU, int mu>
+__device__ __forceinline__ void hop_any(R acc[24], const R v[24], const R u[18], R s, R w) {
+  if constexpr (std::is_same<R, dfloat>::value) hop_term_df<DAGU, mu>(acc, v, u, s, w);
+  else hop_term<R, DAGU, mu>(acc, v, u, s, w);
+}
+// after the hops: lazy double-float sums become dfloats again
+template <typename R>
+__device__ __forceinline__ void hop_finish(R acc[24]) {
+  if constexpr (std::is_same<R, dfloat>::value) {
+#pragma unroll
+    for (int m = 0; m < 24; ++m) acc[m] = df_normalize(acc[m]);
+  }
+}
+
 // (a + i b gamma_5) v, gamma_5 = diag(1,1,-1,-1)
 template <typename R>
 __device__ __forceinline__ void twist_apply(R v[24], R a, R b) {
@@ -524,6 +614,19 @@ __device__ __forceinline__ void block_reduce_cols(double val, int npad, double* 
     for (int w = 0; w < nw; ++w) s += sred[w][threadIdx.x];
     partial[(size_t)threadIdx.x * pstride + blockIdx.x] = s;
   }
+}
+
+// Time slices a contraction covers: t = t0 + k dt for k < ns (all T slices: 0, 1, T).
+// Time-diluted sources (Sec. 2.3) are zero off their slices, so only those are contracted.
+struct Slices {
+  int t0, dt, ns;
+};
+__host__ __device__ __forceinline__ Slices all_slices(int T) { return Slices{0, 1, T}; }
+// index k of slice t in the set, or -1
+__host__ __device__ __forceinline__ int slice_index(const Slices& S, int t) {
+  const int d = t - S.t0;
+  if (d < 0 || d % S.dt != 0 || d / S.dt >= S.ns) return -1;
+  return d / S.dt;
 }
 
 // ---------------------------------------------------------------- host side
@@ -576,4 +679,20 @@ int blocks_for(Batch& B, int threads);  // fills blk_begin, returns the grid siz
 cudaError_t dslash(const Batch& Bin, int prec, int grec, int epi, bool dag, int out_parity, FieldRef in, FieldRef aux,
                    FieldRef out, const GaugeSet& g, const EpiSet& ep, const int* active, double* partial,
                    FieldRef cg_r, FieldRef cg_y, FieldRef cg_p, const double* alpha, cudaStream_t st);
+
+// Stencil launch statistics (process-wide) by class = (storage slot, epilogue, dagger):
+// storage slot 0 double-float, 1 FP32, 2 16-bit, 3 IEEE FP64.  While enabled, every
+// stencil launch outside stream capture is counted and timed with CUDA events (the
+// graph body's launches are counted per replay by the solver: stencil_tally).
+constexpr int DL_SCLASSES = 4 * 4 * 2;
+struct StencilTally {
+  long long n[DL_SCLASSES] = {0};
+};
+void stencil_prof_enable(bool on);    // resets the statistics
+void stencil_prof_sampling(bool on);  // launches that are timed but not counted (extra profiling work)
+void stencil_capture_begin();         // start tallying the launches captured on this thread
+StencilTally stencil_capture_end();
+void stencil_tally_add(const StencilTally& t, long long times);  // graph replays
+// out[class][4] = (launches, timed launches, summed ms, summed site-column items of the timed ones)
+cudaError_t stencil_prof_read(double* out);
 }  // namespace dl

@@ -42,8 +42,9 @@ cudaError_t cg_cond(int ncols, const int* active, const int* flags, int* counter
 // layout (single-lattice batches)
 cudaError_t pack(const Batch& B, int prec, int parity, FieldRef dst, const void* natural, int dtype, cudaStream_t st);
 cudaError_t unpack(const Batch& B, int prec, int parity, void* natural, FieldRef src, int dtype, cudaStream_t st);
+// S (optional): only the sites of these time slices get noise, the rest zero
 cudaError_t noise_z4(const Batch& B, int prec, int parity, FieldRef dst, unsigned long long seed,
-                     unsigned long long first, int quadrant, cudaStream_t st);
+                     unsigned long long first, int quadrant, cudaStream_t st, Slices S = Slices{0, 1, 0});
 cudaError_t pack_gauge(const LatDesc& L, const double* links_dev, void* g64, void* gdf, void* g32, int rec32, void* g16,
                        int rec16, cudaStream_t st);
 
@@ -54,15 +55,17 @@ cudaError_t dft_pass(const double2* in, double2* out, long long nb, int len, lon
                      int fp32, cudaStream_t st);
 // G1 (and the DFT passes' buffers) hold float pairs for P32, double-float pairs for PDF
 // and double pairs for P64; dft_pass / contract_finalize take the kind as fp32 = 1 / 2 / 0
+// S: the time slices covered (all_slices(T), or the slices of a time-diluted source;
+// G1 .. G3 then hold only those slices, finalize writes zeros on the others)
 cudaError_t contract_x(const Batch& B, int prec, int mode, int with_deriv, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                        FieldRef eta_o, const void* g64, const void* g32, int rec32, int mx, double2* phx, double2* G1,
-                       cudaStream_t st);
+                       Slices S, cudaStream_t st);
 cudaError_t contract_finalize(const Batch& B, int with_deriv, int np, const int* mom_dev, int mx, int my, int mz,
                               const double2* G3, int fp32, double pre_re, double pre_im, double2* out, int accumulate,
-                              cudaStream_t st);
+                              Slices S, cudaStream_t st);
 cudaError_t hpe_exact(double kappa, double amu, int flavour, double2* out16, cudaStream_t st);
 cudaError_t add_exact_p0(const Batch& B, int np, int nd, int ip0, const double2* exact16, double scale, double2* out,
-                         cudaStream_t st);
+                         Slices S, cudaStream_t st);
 cudaError_t col_accumulate(const double2* blk, const double2* sub, int ncol, long long per_col, double sign, double2* acc,
                            cudaStream_t st);
 cudaError_t observables(const double2* l1, const double2* l2, int ncol, int T, int np, int nd, int ip0, double* obs,

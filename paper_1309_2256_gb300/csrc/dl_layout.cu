@@ -85,9 +85,10 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
 // Entry (noise r, lex, spin a, colour c) from bits 0 and 1 of
 // splitmix64(seed, (r*V + lex)*12 + 3a + c): (s1 + i s2)/sqrt(2) with
 // s = 1 - 2*bit, or {1, i, -1, -i}[bit0 + 2*bit1] for the quadrant form.
+// Sites on time slices outside S are zero (time-diluted sources, Sec. 2.3).
 template <int P>
 __global__ void noise_kernel(Batch B, int parity, FieldRef dst, unsigned long long seed, unsigned long long first,
-                             int quadrant) {
+                             int quadrant, Slices S) {
   const int l = find_lat(B, blockIdx.x);
   const LatDesc& L = B.lat[l];
   const int npad = 1 << L.lognpad;
@@ -97,9 +98,9 @@ __global__ void noise_kernel(Batch B, int parity, FieldRef dst, unsigned long lo
   const int col = (int)(j & (npad - 1));
   const int i = (int)(j >> L.lognpad);
   typename SIO<P>::real v[24];
-  if (col < L.ncol) {
-    int x, y, z, t;
-    cb_coords(L, i, parity, x, y, z, t);
+  int x, y, z, t;
+  cb_coords(L, i, parity, x, y, z, t);
+  if (col < L.ncol && slice_index(S, t) >= 0) {
     const unsigned long long V = 2ULL * (unsigned long long)L.Vh;
     const unsigned long long r = first + (unsigned long long)L.noise_base + (unsigned long long)col;
     const unsigned long long n0 = (r * V + (unsigned long long)lex_of(L, x, y, z, t)) * 12ULL;
@@ -225,12 +226,13 @@ cudaError_t unpack(const Batch& B, int prec, int parity, void* natural, FieldRef
 }
 
 cudaError_t noise_z4(const Batch& Bin, int prec, int parity, FieldRef dst, unsigned long long seed,
-                     unsigned long long first, int quadrant, cudaStream_t st) {
+                     unsigned long long first, int quadrant, cudaStream_t st, Slices S) {
   Batch B = Bin;
   int g = blocks_for(B, 256);
   if (!g) return cudaSuccess;
+  if (S.ns == 0) S = Slices{0, 1, 1 << 30};  // every slice
   DL_COUNT();
-  DISPATCH_P(prec, (noise_kernel<PP><<<g, 256, 0, st>>>(B, parity, dst, seed, first, quadrant)));
+  DISPATCH_P(prec, (noise_kernel<PP><<<g, 256, 0, st>>>(B, parity, dst, seed, first, quadrant, S)));
   return cudaGetLastError();
 }
 

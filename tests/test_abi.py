@@ -60,6 +60,7 @@ NULL_HANDLE_CALLS = {
     "dl_apply_noalloc": (None, 0, 0, 1, 1, None, None, None, 0),
     "dl_solve": (None, None, None, 1, 0, None, None),
     "dl_contract": (None, 0, None, None, 1, 0, 0, 0, None, 0),
+    "dl_contract_slices": (None, 0, None, None, 1, 0, 0, 0, 1, None, 0),
     "dl_hpe_exact": (None, 1, None),
     "dl_tsm_run": (None, None, None, None, None, None, None),
     "dl_load_gauge_lat": (None, 0, None, 0, -1.0, 12, 12),
@@ -80,7 +81,7 @@ NULL_HANDLE_CALLS = {
     "dl_store_count": (None, None),
 }
 # calls without a handle argument, or whose NULL handle is a no-op by definition
-NO_HANDLE = {"dl_create", "dl_momenta", "dl_kernel_launches", "dl_destroy", "dl_nn_destroy", "dl_last_error",
+NO_HANDLE = {"dl_create", "dl_momenta", "dl_kernel_launches", "dl_profile_stencils", "dl_destroy", "dl_nn_destroy", "dl_last_error",
              "dl_nn_weight_count", "dl_store_last_error", "dl_store_open", "dl_store_close", "dl_store_load",
              "dl_store_sources"}
 
@@ -95,3 +96,4 @@ def test_null_handles_are_rejected():
     h.dl_nn_destroy(None)
     assert h.dl_nn_weight_count(None) == 0
     assert h.dl_last_error(None) is not None
+    assert h.dl_profile_stencils(None) == dl.DL_ERR_ARG

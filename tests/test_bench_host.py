@@ -1,7 +1,5 @@
 """Host logic of bench.py (no GPU): the equal-error metric (the paper's cost x error^2
 figure of merit, Sec. 4) and the roofline arithmetic of the dominant stencil launch."""
-import types
-
 import numpy as np
 import pytest
 
@@ -41,22 +39,36 @@ def test_equal_error_useless_lp_map():
     assert abs(e["r_c"]) < 0.05
 
 
-def test_roofline_bytes_of_the_16bit_stage3_launch():
-    """Algorithmic bytes of one 16-bit stage-3 launch on 32^3 x 64 with 16 columns:
-    all 4V links once (24 B, 16-bit recon-12) plus 7 spinor streams of Vh x 16 x 52 B."""
+def test_roofline_picks_the_class_with_the_most_time_per_sweep():
+    """Stencil statistics of two steps: a 16-bit CG-update class (7 spinor streams) with
+    many short launches and a double-float class with few long ones.  The roofline
+    kernel is the class with the larger launches x average duration; its algorithmic
+    bytes are all 4V links once plus every spinor stream of Vh x columns once."""
     V = 32 ** 3 * 64
     Vh = V // 2
-    prof = np.zeros((4, 3, 3))
-    prof[3, 2] = (10, 10 * 1.6, 10 * Vh * 16)  # 10 launches of 1.6 ms, 16 columns each
-    prof[0, 1] = (10, 10 * 0.5, 10 * Vh * 16)
-    infos = [types.SimpleNamespace(iters_hp=24 * 44, iters_lp=524 * 40)]
-    r = bench.roofline(prof, infos)
+    st = np.zeros((4, 4, 2, 4))
+    # 16-bit (storage 2), cg-update (epilogue 3), dagger: 600 launches, 20 timed at 1.6 ms, 16 columns
+    st[2, 3, 1] = (600, 20, 20 * 1.6, 20 * Vh * 16)
+    # double-float (storage 0), plain, not dagger: 40 launches, 10 timed at 5 ms, 16 columns
+    st[0, 0, 0] = (40, 10, 10 * 5.0, 10 * Vh * 16)
+    r, rows = bench.roofline(st, steps=2)
+    assert [x["kernel"] for x in rows] == ["stencil 16-bit cg-update dagger", "stencil double-float plain"]
+    assert rows[0]["ms_per_step"] == pytest.approx(600 * 1.6 / 2)
+    assert rows[1]["ms_per_step"] == pytest.approx(40 * 5.0 / 2)
     expect = 4 * V * 24 + 7 * Vh * 16 * 52
+    assert r["kernel"] == "stencil 16-bit cg-update dagger"
     assert r["bytes_per_launch"] == expect
     assert r["avg_launch_ms"] == pytest.approx(1.6)
     assert r["achieved"] == pytest.approx(expect / 1.6e-3 / 1e9, rel=1e-3)
     peaks, _ = bench._peaks()
     assert r["frac"] == pytest.approx(r["achieved"] / peaks["hbm_gbs"], rel=1e-3)
-    # the ncu traffic of the 24^3 x 24 capture, scaled by site-columns
-    assert r["traffic"] == int(1002.4e6 / (24 ** 4 // 2 * 16) * Vh * 16)
+    assert rows[1]["bytes_per_launch"] == 4 * V * 144 + 2 * Vh * 16 * 192
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
+def test_gamma_matrices_of_the_error_report():
+    """The error report forms loops with its own 16 Gamma_b; they are the oracle's."""
+    from oracle import lattice
+    g = bench._gammas16()
+    for b in range(16):
+        assert np.abs(g[b] - lattice.GAMMAS16[b]).max() == 0.0

@@ -26,6 +26,19 @@ void df_dot(int n, const float* a, const float* b, float* o) {
   for (int i = 0; i < n; ++i) acc += dfloat(a[2 * i], a[2 * i + 1]) * dfloat(b[2 * i], b[2 * i + 1]);
   o[0] = acc.hi; o[1] = acc.lo;
 }
+// the stencil's lazy sums: products accumulated unnormalised, normalised once
+void df_dot_lazy(int n, const float* a, const float* b, float* o) {
+  dfloat acc = df_mul_lazy(dfloat(a[0], a[1]), dfloat(b[0], b[1]));
+  for (int i = 1; i < n; ++i) df_acc_mul(acc, dfloat(a[2 * i], a[2 * i + 1]), dfloat(b[2 * i], b[2 * i + 1]));
+  acc = df_normalize(acc);
+  o[0] = acc.hi; o[1] = acc.lo;
+}
+void df_sum_lazy(int n, const float* a, float* o) {
+  dfloat acc = df_add_lazy(dfloat(a[0], a[1]), dfloat(a[2], a[3]));
+  for (int i = 2; i < n; ++i) df_acc(acc, dfloat(a[2 * i], a[2 * i + 1]));
+  acc = df_normalize(acc);
+  o[0] = acc.hi; o[1] = acc.lo;
+}
 }
 """
 
@@ -109,3 +122,38 @@ def test_dot_product_of_200_terms(lib):
         ex = sum(_exact(a[2 * i:2 * i + 2]) * _exact(b[2 * i:2 * i + 2]) for i in range(n))
         mag = sum(abs(_exact(a[2 * i:2 * i + 2]) * _exact(b[2 * i:2 * i + 2])) for i in range(n))
         assert abs(_exact(o) - ex) <= mag * Fraction(1, 2 ** 46)
+
+
+@pytest.mark.parametrize("n", [3, 6, 8, 48])
+def test_lazy_dot_products(lib, n):
+    """The stencil's SU(3) sums (6 products per output) accumulated without intermediate
+    normalisation, normalised (|lo| <= ulp(hi)/2) at the end.  The unnormalised low part
+    grows with the terms added, each FP32 addition into it erring by 2^-24 of it, so the
+    error bound is linear in the length: (n + 2) 2^-48 of the sum of the magnitudes
+    (6 terms: 2^-45)."""
+    rng = random.Random(5 + n)
+    for _ in range(1000):
+        a = [c for _ in range(n) for c in _split(lib, rng.uniform(-1, 1) * 10 ** rng.randint(-2, 2))]
+        b = [c for _ in range(n) for c in _split(lib, rng.uniform(-1, 1))]
+        o = _f2([0.0, 0.0])
+        lib.df_dot_lazy(n, _f2(a), _f2(b), o)
+        ex = sum(_exact(a[2 * i:2 * i + 2]) * _exact(b[2 * i:2 * i + 2]) for i in range(n))
+        mag = sum(abs(_exact(a[2 * i:2 * i + 2]) * _exact(b[2 * i:2 * i + 2])) for i in range(n))
+        assert abs(_exact(o) - ex) <= mag * Fraction(n + 2, 2 ** 48)
+        assert abs(o[1]) <= abs(o[0]) * 2.0 ** -23
+
+
+def test_lazy_sum_with_cancellation(lib):
+    """The hop sum of the stencil (eight terms of either sign that may nearly cancel):
+    absolute error within 2^-47 of the summed magnitudes, also when the result is far
+    smaller than the terms."""
+    rng = random.Random(6)
+    for k in range(300):
+        x = [rng.uniform(-1, 1) for _ in range(7)]
+        x.append(-sum(x) + (rng.uniform(-1, 1) * 1e-9 if k % 2 else 0.0))  # near or exact cancellation
+        a = [c for v in x for c in _split(lib, v)]
+        o = _f2([0.0, 0.0])
+        lib.df_sum_lazy(len(x), _f2(a), o)
+        ex = sum(_exact(a[2 * i:2 * i + 2]) for i in range(len(x)))
+        mag = sum(abs(_exact(a[2 * i:2 * i + 2])) for i in range(len(x)))
+        assert abs(_exact(o) - ex) <= mag * Fraction(1, 2 ** 47)
