@@ -515,25 +515,27 @@ cudaError_t dslash(const Batch& Bin, int prec, int grec, int epi, bool dag, int 
   StencilProf& P = sprof();
   const int cls = stencil_class(prec, epi, dag);
   if (t_capturing) t_tally.n[cls] += 1;
-  bool timed = false;
+  const bool prof = P.on && !t_capturing;
+  bool started = false;  // the start event is recorded
   TimedLaunch tl{nullptr, nullptr, cls, 0};
-  if (P.on && !t_capturing) {
+  if (prof) {
     for (int l = 0; l < Bin.nlat; ++l) tl.items += (long long)Bin.lat[l].Vh * Bin.lat[l].ncol;
     if (cudaEventCreate(&tl.e0) == cudaSuccess && cudaEventCreate(&tl.e1) == cudaSuccess &&
         cudaEventRecord(tl.e0, st) == cudaSuccess)
-      timed = true;
+      started = true;
   }
   cudaError_t e = dslash_launch(Bin, prec, grec, epi, dag, out_parity, in, aux, out, g, ep, active, partial, cr, cy, cp,
                                 alpha, st);
-  if (P.on && !t_capturing) {
+  bool queued = false;  // the event pair now belongs to the pending list
+  if (prof) {
     std::lock_guard<std::mutex> lk(P.mu);
     if (!t_sampling) P.n[cls] += 1;
-    if (timed && e == cudaSuccess && cudaEventRecord(tl.e1, st) == cudaSuccess) {
+    if (started && e == cudaSuccess && cudaEventRecord(tl.e1, st) == cudaSuccess) {
       P.pending.push_back(tl);
-      timed = false;
+      queued = true;
     }
   }
-  if (timed || (tl.e0 && !timed)) {  // not handed over: release the events
+  if (!queued) {  // release events that were created but not handed over
     if (tl.e0) cudaEventDestroy(tl.e0);
     if (tl.e1) cudaEventDestroy(tl.e1);
   }
