@@ -16,7 +16,9 @@ G(x+mu)^+, x_i -> G x_i implies y_o -> G y_o.  The network is a stack of layers
 (1 -> C -> ... -> C -> 1 channels); with no nonlinearity it is a linear map, and
 four layers reach four hops.
 
-Training loss over pairs (eta_k, s_k): sum_k |N(eta_k) - s_k|^2 / |s_k|^2.
+Training loss over pairs (eta_k, s_k): sum_k |N(eta_k) - s_k|^2 / |s_k|^2, or the
+residual loss sum_k |M N(eta_k) - eta_k|^2 / |eta_k|^2 (no solution needed; it weighs
+the error of N by M itself, i.e. every mode of M N - 1 alike).
 Gradients use the Wirtinger convention: for a real loss L and complex weight w,
 grad(w) = dL/d(conj w) * 2 = 2 sum (conj(input feature) * output gradient), where
 the output gradient g = dL/d(conj y) = (y - s) / |s|^2.
@@ -128,6 +130,26 @@ def loss_and_grads(links, weights, pairs, bc=-1.0):
         d = out - s
         total += np.vdot(d, d).real / ns
         g = (d / ns)[None]
+        for li in range(len(weights) - 1, -1, -1):
+            gw, g = layer_backward(links, weights[li], inputs[li], g, bc)
+            for k in gw:
+                grads[li][k] += gw[k]
+    return total, grads
+
+
+def residual_loss_and_grads(links, weights, etas, kappa, amu, f=1, bc=-1.0):
+    """Loss sum_k |M_f N(eta_k) - eta_k|^2 / |eta_k|^2 and its Wirtinger gradients.
+
+    With r = M y - eta, y = N(eta), the output gradient is dL/d(conj y) = M^+ r / |eta|^2,
+    which the layers propagate back exactly as for the solution loss."""
+    total = 0.0
+    grads = [{k: np.zeros_like(v) for k, v in w.items()} for w in weights]
+    for eta in etas:
+        out, inputs = forward(links, weights, eta, bc)
+        ne = np.vdot(eta, eta).real
+        r = op.apply_m(links, out, kappa, amu, f, bc) - eta
+        total += np.vdot(r, r).real / ne
+        g = (op.apply_m_dag(links, r, kappa, amu, f, bc) / ne)[None]
         for li in range(len(weights) - 1, -1, -1):
             gw, g = layer_backward(links, weights[li], inputs[li], g, bc)
             for k in gw:

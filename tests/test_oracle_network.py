@@ -38,6 +38,44 @@ def test_gradients_match_finite_differences():
     assert checked == 12
 
 
+def test_residual_loss_gradients_match_finite_differences():
+    """The residual loss |M N eta - eta|^2 / |eta|^2: Wirtinger gradients against central
+    differences of the loss itself."""
+    rng = np.random.default_rng(2)
+    links = synth.gauge_links(DIMS, 0.4, 85)
+    weights = _small_net(rng)
+    etas = [noise.z4_noise(DIMS, 7, r) for r in range(2)]
+    _, grads = network.residual_loss_and_grads(links, weights, etas, KAPPA, AMU)
+    h = 1e-6
+    for li, key, idx in [(0, "W0", (1, 0, 0)), (1, "Wf", (1, 2, 0, 1)), (1, "Wb", (0, 0, 2, 3)), (2, "Wb", (3, 0, 1, 2))]:
+        for part in (1.0, 1j):
+            w_p = [{k: v.copy() for k, v in w.items()} for w in weights]
+            w_m = [{k: v.copy() for k, v in w.items()} for w in weights]
+            w_p[li][key][idx] += part * h
+            w_m[li][key][idx] -= part * h
+            lp, _ = network.residual_loss_and_grads(links, w_p, etas, KAPPA, AMU)
+            lm, _ = network.residual_loss_and_grads(links, w_m, etas, KAPPA, AMU)
+            fd = (lp - lm) / (2 * h)
+            an = grads[li][key][idx].real if part == 1.0 else grads[li][key][idx].imag
+            assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3), (li, key, idx, part, fd, an)
+
+
+def test_residual_loss_vanishes_at_the_inverse_and_equals_the_solution_loss_weighted():
+    """At N = M^-1 (dense, on a tiny lattice through a one-layer stand-in) the residual
+    is zero; and for any map y the residual loss equals |M (y - s)|^2 / |eta|^2 with
+    s = M^-1 eta (the solution error weighted by M)."""
+    links = synth.gauge_links(DIMS, 0.4, 86)
+    eta = noise.z4_noise(DIMS, 8, 0)
+    m = op.dense_matrix(links, KAPPA, AMU, 1)
+    s = np.linalg.solve(m, eta.ravel()).reshape(eta.shape)
+    r = op.apply_m(links, s, KAPPA, AMU) - eta
+    assert np.vdot(r, r).real / np.vdot(eta, eta).real < 1e-24
+    y = synth.gaussian_spinors(DIMS, 1, 87)[0]
+    r = op.apply_m(links, y, KAPPA, AMU) - eta
+    e = op.apply_m(links, y - s, KAPPA, AMU)
+    assert abs(np.vdot(r, r).real - np.vdot(e, e).real) < 1e-10 * np.vdot(e, e).real
+
+
 def test_gauge_equivariance():
     rng = np.random.default_rng(1)
     links = synth.gauge_links(DIMS, 0.4, 82)
