@@ -590,9 +590,12 @@ def learned_case(args):
 
     def progress(what):
         print(f"[learned {time.perf_counter() - t_start:8.1f} s] {what}", file=sys.stderr, flush=True)
-    # training pairs from the plain solver (complex64 storage, FP64-accurate solutions)
+    # training pairs from the plain solver (complex64 storage, FP64-accurate solutions); the
+    # residual loss needs the noise only
+    residual = args.nn_loss == "residual"
+    out["loss"] = args.nn_loss
     eta = torch.empty((args.pairs, V * 12), dtype=torch.complex64, device="cuda")
-    sol = torch.empty_like(eta)
+    sol = None if residual else torch.empty_like(eta)
     hp = dl.dl_solve_params(tol=1e-10, max_iter=100000, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.01, flavour=1,
                             chunk=0)
     torch.cuda.synchronize()
@@ -600,14 +603,15 @@ def learned_case(args):
     for b in range(0, args.pairs, 32):
         n = min(32, args.pairs - b)
         dl.dl_noise_z4(ctx, 2000 + cfg["id"], b, n, eta[b:b + n], dl.DL_C64)
-        dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
+        if not residual:
+            dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
     torch.cuda.synchronize()
     out["seconds_pairs"] = time.perf_counter() - t0
-    progress(f"{args.pairs} training pairs")
+    progress(f"{args.pairs} training sources" + ("" if residual else " with solutions"))
     nn = dl.dl_nn_create(ctx, 4, 16, dl.DL_BF16)
     dl.dl_nn_set_weights(nn, synth.network_weights(4, 16, 3000 + cfg["id"]))
     tp = dl.dl_nn_train_params(steps=args.train_steps, batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,
-                               seed=11)
+                               seed=11, loss=1 if residual else 0)
     t0 = time.perf_counter()
     hist = dl.dl_nn_train(nn, tp, args.pairs, eta, sol, dl.DL_C64)
     torch.cuda.synchronize()
@@ -759,8 +763,11 @@ def mass_case(args):
             t_lp = info.seconds_lp / (n_hp + n_lp)
             t_c = info.seconds_contract / (2 * n_hp + n_lp)
             key = "one_deriv" if deriv else "local"
+            # Table compAll analogue: the contractions are the mass-independent overhead
+            # (OH) next to the inversion cost of one HP and one LP estimate
             row[key] = {"r_hp_lp": (t_hp + t_c) / (t_lp + t_c), "sec_hp_solve": t_hp, "sec_lp_solve": t_lp,
-                        "sec_contract_per_solution": t_c, "iters_hp": info.iters_hp / n_hp,
+                        "sec_contract_per_solution": t_c, "overhead_share_hp": t_c / (t_hp + t_c),
+                        "overhead_share_lp": t_c / (t_lp + t_c), "iters_hp": info.iters_hp / n_hp,
                         "iters_lp": info.iters_lp / (n_hp + n_lp), "not_converged": info.not_converged}
         rows.append(row)
     dl.dl_destroy(ctx)
@@ -869,6 +876,8 @@ def main():
     ap.add_argument("--fgcr-max-iter", type=int, default=600, help="learned case: FGCR iterations per solve")
     ap.add_argument("--batch", type=int, default=4, help="learned case: pairs per Adam step")
     ap.add_argument("--lr", type=float, default=1e-3, help="learned case: Adam learning rate")
+    ap.add_argument("--nn-loss", default="solution", choices=["solution", "residual"],
+                    help="learned case: training loss |N eta - s|^2/|s|^2 or |M N eta - eta|^2/|eta|^2")
     ap.add_argument("--masses", default="0.0055,0.02,0.2", help="mass case: valence a*mu values")
     args = ap.parse_args()
     if args.case == "mass":

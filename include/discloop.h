@@ -403,11 +403,19 @@ dl_status dl_nn_apply_adjoint(dl_nn* nn, int n, const void* in, void* out, int d
 dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int dtype, double* loss,
                           float* grad);
 
+/* The residual loss sum_k |M_u N(eta_k) - eta_k|^2 / |eta_k|^2 over n sources (device
+ * natural fields) and its gradient (as dl_nn_loss_grad: 2 dL/d conj(W), host complex64);
+ * the operator is applied in FP32 with the context's kappa, a*mu and FP32 links. */
+dl_status dl_nn_loss_grad_residual(dl_nn* nn, int n, const void* eta, int dtype, double* loss, float* grad);
+
 typedef struct {
   int steps;            /* Adam steps */
   int batch;            /* pairs per step (mean loss) */
   double lr, beta1, beta2, eps;
   uint64_t seed;        /* order of the pairs: a seeded shuffle per pass */
+  int loss;             /* 0: |N eta - s|^2 / |s|^2 over (eta, s) pairs; 1: the residual
+                           |M_u N eta - eta|^2 / |eta|^2 (s may be NULL), which weighs the
+                           error of N by M itself rather than by M^-1 */
 } dl_nn_train_params;
 
 /* Adam on the mean loss over minibatches of the n_pairs (eta, s) pairs (device

@@ -65,7 +65,7 @@ class dl_batch_info(C.Structure):
 
 class dl_nn_train_params(C.Structure):
     _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("beta1", C.c_double),
-                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
+                ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64), ("loss", C.c_int)]
 
 
 class dl_fgcr_params(C.Structure):
@@ -122,6 +122,7 @@ _SIGS = {
     "dl_nn_apply": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "dl_nn_apply_adjoint": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "dl_nn_loss_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "dl_nn_loss_grad_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "dl_nn_train": (C.c_int, [C.c_void_p, C.POINTER(dl_nn_train_params), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                               C.c_void_p]),
     "dl_fgcr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(dl_fgcr_params), C.c_int, C.c_void_p, C.c_void_p,
@@ -366,6 +367,15 @@ def dl_nn_loss_grad(nn, n, eta, s, dtype=DL_C128):
     grad = np.zeros(dl_nn_weight_count(nn), dtype=np.complex64)
     _check(nn["ctx"], lib().dl_nn_loss_grad(nn["h"], int(n), _ptr(eta), _ptr(s), int(dtype), loss.ctypes.data,
                                             grad.ctypes.data))
+    return float(loss[0]), grad
+
+
+def dl_nn_loss_grad_residual(nn, n, eta, dtype=DL_C128):
+    """Residual loss sum_k |M_u N(eta_k) - eta_k|^2 / |eta_k|^2 and its gradient (weight layout)."""
+    loss = np.zeros(1, dtype=np.float64)
+    grad = np.zeros(dl_nn_weight_count(nn), dtype=np.complex64)
+    _check(nn["ctx"], lib().dl_nn_loss_grad_residual(nn["h"], int(n), _ptr(eta), int(dtype), loss.ctypes.data,
+                                                     grad.ctypes.data))
     return float(loss[0]), grad
 
 

@@ -190,9 +190,11 @@ dl_status target_norms(dl_nn* nn, int n, const void* s, int dtype, std::vector<d
 
 // Forward, loss and backward of the pairs idx[0..n) with inverse target norms
 // inv_dev (device, per listed pair); weight-gradient partials accumulate in
-// nn->wpart.  Returns the summed loss of the pairs.
+// nn->wpart.  Returns the summed loss of the pairs.  kind 0: |N eta - s|^2 / |s|^2;
+// kind 1 (residual, s unused, inv = 1 / |eta|^2): |M_u N eta - eta|^2 / |eta|^2, whose
+// output gradient M_u^+ (M_u y - eta) / |eta|^2 is formed in FP32 with the stencil.
 dl_status loss_grad_pairs(dl_nn* nn, const void* eta, const void* s, int dtype, const int* idx, int n,
-                          const double* inv_dev, const std::vector<double>& inv_host, double* loss) {
+                          const double* inv_dev, const std::vector<double>& inv_host, double* loss, int kind = 0) {
   dl_ctx* c = nn->c;
   dl_status st;
   Acts X, G;
@@ -208,13 +210,45 @@ dl_status loss_grad_pairs(dl_nn* nn, const void* eta, const void* s, int dtype, 
     nn->nloss = 2 * n;
   }
   double* lossd = nn->dscal + 2;
+  Field *ye = nullptr, *yo = nullptr, *me = nullptr, *mo = nullptr, *ze = nullptr, *zo = nullptr;
+  if (kind == 1) {
+    if ((st = ensure_field(c, "nn_ye", P32, B1, &ye)) || (st = ensure_field(c, "nn_yo", P32, B1, &yo)) ||
+        (st = ensure_field(c, "nn_me", P32, B1, &me)) || (st = ensure_field(c, "nn_mo", P32, B1, &mo)) ||
+        (st = ensure_field(c, "nn_ze", nn->act, B1, &ze)) || (st = ensure_field(c, "nn_zo", nn->act, B1, &zo)))
+      return st;
+    CK(dl::zero(B1, nn->act, ze->ref(), nullptr, c->st));
+    CK(dl::zero(B1, nn->act, zo->ref(), nullptr, c->st));
+  }
+  GaugeSet g{c->g64, c->g32, c->g16};
+  const EpiSet Em = epiB(B1, CK_MK, 0, 0, 1, 1);    // out_p = R_u in_p - kappa D in_{1-p}: M_u
+  const EpiSet Ed = epiB(B1, CK_MK, 0, 0, 1, -1);   // M_u^+ (dagger projectors)
   for (int q = 0; q < n; ++q) {
-    if ((st = pack_pair(nn, eta, s, dtype, idx[q], X, se, so)) != DL_OK) return st;
+    if ((st = pack_pair(nn, eta, kind == 1 ? eta : s, dtype, idx[q], X, se, so)) != DL_OK) return st;
     if ((st = forward(nn, X)) != DL_OK) return st;
-    for (int p = 0; p < 2; ++p) {
-      CK(dl::nn_lossgrad(B1, nn->act, p ? X.o[nn->nl]->ref() : X.e[nn->nl]->ref(), p ? so->ref() : se->ref(),
-                         p ? G.o[nn->nl]->ref() : G.e[nn->nl]->ref(), inv_dev + q, c->partial, c->st));
-      CK(dl::sum_partials(B1, c->partial, lossd + 2 * q + p, 0, 0, 1, c->st));
+    if (kind == 0) {
+      for (int p = 0; p < 2; ++p) {
+        CK(dl::nn_lossgrad(B1, nn->act, p ? X.o[nn->nl]->ref() : X.e[nn->nl]->ref(), p ? so->ref() : se->ref(),
+                           p ? G.o[nn->nl]->ref() : G.e[nn->nl]->ref(), inv_dev + q, c->partial, c->st));
+        CK(dl::sum_partials(B1, c->partial, lossd + 2 * q + p, 0, 0, 1, c->st));
+      }
+    } else {
+      // y in FP32; m = eta - M_u y (|m|^2 is the loss); then G = (0 - M_u^+ m) / |eta|^2
+      CK(dl::copy(B1, P32, nn->act, ye->ref(), X.e[nn->nl]->ref(), nullptr, c->st));
+      CK(dl::copy(B1, P32, nn->act, yo->ref(), X.o[nn->nl]->ref(), nullptr, c->st));
+      CK(dl::dslash(B1, P32, c->rec32, EPI_AUX, false, 0, yo->ref(), ye->ref(), me->ref(), g, Em, nullptr, nullptr, NOF,
+                    NOF, NOF, nullptr, c->st));
+      CK(dl::dslash(B1, P32, c->rec32, EPI_AUX, false, 1, ye->ref(), yo->ref(), mo->ref(), g, Em, nullptr, nullptr, NOF,
+                    NOF, NOF, nullptr, c->st));
+      CK(dl::xmy_norm(B1, P32, me->ref(), se->ref(), me->ref(), nullptr, c->partial, c->st));
+      CK(dl::sum_partials(B1, c->partial, lossd + 2 * q, 0, 0, 1, c->st));
+      CK(dl::xmy_norm(B1, P32, mo->ref(), so->ref(), mo->ref(), nullptr, c->partial, c->st));
+      CK(dl::sum_partials(B1, c->partial, lossd + 2 * q + 1, 0, 0, 1, c->st));
+      CK(dl::dslash(B1, P32, c->rec32, EPI_AUX, true, 0, mo->ref(), me->ref(), ye->ref(), g, Ed, nullptr, nullptr, NOF,
+                    NOF, NOF, nullptr, c->st));
+      CK(dl::dslash(B1, P32, c->rec32, EPI_AUX, true, 1, me->ref(), mo->ref(), yo->ref(), g, Ed, nullptr, nullptr, NOF,
+                    NOF, NOF, nullptr, c->st));
+      CK(dl::nn_lossgrad(B1, nn->act, ze->ref(), ye->ref(), G.e[nn->nl]->ref(), inv_dev + q, c->partial, c->st));
+      CK(dl::nn_lossgrad(B1, nn->act, zo->ref(), yo->ref(), G.o[nn->nl]->ref(), inv_dev + q, c->partial, c->st));
     }
     if ((st = backward(nn, X, G)) != DL_OK) return st;
   }
@@ -423,18 +457,46 @@ dl_status dl_nn_loss_grad(dl_nn* nn, int n, const void* eta, const void* s, int 
   return leave(c);
 } DL_CATCH((nn ? nn->c : nullptr))
 
+dl_status dl_nn_loss_grad_residual(dl_nn* nn, int n, const void* eta, int dtype, double* loss, float* grad) try {
+  if (!valid_nn(nn)) return DL_ERR_ARG;
+  dl_ctx* c = nn->c;
+  if (!eta || n < 1 || (dtype != DL_C128 && dtype != DL_C64))
+    return fail(c, DL_ERR_ARG, "dl_nn_loss_grad_residual: bad argument");
+  dl_status st;
+  if ((st = enter(c)) != DL_OK) return st;
+  std::vector<double> inv;
+  if ((st = target_norms(nn, n, eta, dtype, inv)) != DL_OK) return st;
+  void* p;
+  if ((st = ensure_buf(c, "nn_inv", sizeof(double) * n, &p)) != DL_OK) return st;
+  double* inv_dev = (double*)p;
+  CK(cudaMemcpyAsync(inv_dev, inv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  std::vector<int> idx(n);
+  for (int k = 0; k < n; ++k) idx[k] = k;
+  if ((st = zero_wpart(nn)) != DL_OK) return st;
+  double L = 0.0;
+  if ((st = loss_grad_pairs(nn, eta, nullptr, dtype, idx.data(), n, inv_dev, inv, &L, 1)) != DL_OK) return st;
+  if ((st = reduce_grad(nn)) != DL_OK) return st;
+  if (grad) CK(cudaMemcpyAsync(grad, nn->grad, sizeof(float2) * nn->nw, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (loss) *loss = L;
+  if ((st = check_tc(nn)) != DL_OK) return st;
+  return leave(c);
+} DL_CATCH((nn ? nn->c : nullptr))
+
 dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, const void* eta, const void* s, int dtype,
                       double* loss_hist) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
   if (!prm || !eta || !s || n_pairs < 1 || prm->steps < 0 || prm->batch < 1 || prm->batch > n_pairs ||
       !(prm->lr > 0.0) || !(prm->beta1 >= 0.0 && prm->beta1 < 1.0) || !(prm->beta2 >= 0.0 && prm->beta2 < 1.0) ||
-      !(prm->eps > 0.0) || (dtype != DL_C128 && dtype != DL_C64))
+      !(prm->eps > 0.0) || (dtype != DL_C128 && dtype != DL_C64) || (prm->loss != 0 && prm->loss != 1) ||
+      (prm->loss == 0 && !s))
     return fail(c, DL_ERR_ARG, "dl_nn_train: bad parameters");
   dl_status st;
   if ((st = enter(c)) != DL_OK) return st;
   std::vector<double> inv;
-  if ((st = target_norms(nn, n_pairs, s, dtype, inv)) != DL_OK) return st;
+  // 1 / |s|^2 for the solution loss, 1 / |eta|^2 for the residual loss
+  if ((st = target_norms(nn, n_pairs, prm->loss == 1 ? eta : s, dtype, inv)) != DL_OK) return st;
   void* p;
   if ((st = ensure_buf(c, "nn_inv", sizeof(double) * n_pairs, &p)) != DL_OK) return st;
   double* inv_all = (double*)p;
@@ -467,7 +529,7 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, con
     }
     if ((st = zero_wpart(nn)) != DL_OK) return st;
     double L = 0.0;
-    if ((st = loss_grad_pairs(nn, eta, s, dtype, idx.data(), prm->batch, inv_b, invh, &L)) != DL_OK) return st;
+    if ((st = loss_grad_pairs(nn, eta, s, dtype, idx.data(), prm->batch, inv_b, invh, &L, prm->loss)) != DL_OK) return st;
     if ((st = reduce_grad(nn)) != DL_OK) return st;
     nn->adam_t += 1;
     CK(dl::nn_adam(nn->W, nn->grad, nn->m, nn->v, nn->nw, (float)prm->lr, (float)prm->beta1, (float)prm->beta2,

@@ -75,6 +75,7 @@ NULL_HANDLE_CALLS = {
     "dl_nn_apply_adjoint": (None, 1, None, None, 0),
     "dl_nn_loss_grad": (None, 1, None, None, 0, None, None),
     "dl_nn_train": (None, None, 1, None, None, 0, None),
+    "dl_nn_loss_grad_residual": (None, 1, None, 0, None, None),
     "dl_fgcr_solve": (None, None, None, 1, None, None, 0, None),
     "dl_create_multi": (None, 1, None, 0, None),
     "dl_store_add": (None, None, 1),

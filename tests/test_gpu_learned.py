@@ -173,6 +173,29 @@ def test_loss_and_gradients_match_oracle(dl):
     assert np.abs(grad - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
+def test_residual_loss_and_gradients_match_oracle(dl):
+    """The residual loss |M_u N eta - eta|^2 / |eta|^2 of three sources and every weight
+    gradient, FP32 activations, against the oracle (M applied in FP32 on the GPU)."""
+    dims = (4, 4, 2, 4)
+    n_layers, c = 3, 4
+    kappa, amu = 0.16, 0.01
+    links = synth.gauge_links(dims, 0.4, 315)
+    w = synth.network_weights(n_layers, c, 60, scale=0.8, identity=0.7)
+    eta = np.stack([noise.z4_noise(dims, 14, r) for r in range(3)])
+    ctx = _ctx(dl, dims, links, kappa, amu)
+    try:
+        nn = dl.dl_nn_create(ctx, n_layers, c, dl.DL_F32)
+        dl.dl_nn_set_weights(nn, w)
+        loss, grad = dl.dl_nn_loss_grad_residual(nn, 3, _dev(eta))
+        dl.dl_nn_destroy(nn)
+    finally:
+        dl.dl_destroy(ctx)
+    ref_loss, ref_grads = network.residual_loss_and_grads(links, _to_oracle(w, n_layers, c), list(eta), kappa, amu)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    ref = _from_oracle(ref_grads)
+    assert np.abs(grad - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
 def test_gauge_equivariance_on_gpu(dl):
     """N[U^G](G eta) = G N[U](eta) for a random SU(3) gauge transformation G."""
     dims = (4, 4, 4, 4)
