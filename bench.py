@@ -397,10 +397,10 @@ def roofline(st, steps):
 # proportion to the volume.  One worker process per host core, each on its own
 # noise vector, single-threaded numpy.
 SAMPLE_T = 2
-# CG iterations of one plain FP64 solve from zero to 1e-10 at this workload: the
-# batched FP64 comparator of the GPU arm measures the same quantity on every run
-# (detail.plain_fp64_batched.iters) to check this value.
-PLAIN_CG_ITERS = 50.0
+# CG iterations of one plain FP64 solve from zero to 1e-10 at this workload, as the
+# batched FP64 comparator of the GPU arm measures them (detail.plain_fp64_batched.iters,
+# the same on every run: 52 in double-float and in IEEE binary64).
+PLAIN_CG_ITERS = 52.0
 _SAMPLE = {}
 
 

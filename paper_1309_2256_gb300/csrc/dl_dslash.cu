@@ -141,15 +141,26 @@ __global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : DL_
     R acc[24];
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] = 0;
+    if constexpr (std::is_same<R, dfloat>::value) {
+      // one body for the eight hops (runtime direction): the code fits the instruction cache
+#pragma unroll 1
+      for (int d = 0; d < 8; ++d) {
+        R v[24], w;
+        load_hop<P>(inb, inn, nitems, ((long long)snb[d * S + sl] << lg) + col, v, w);
+        hop_term_df_rt(acc, v, su + (d * S + sl) * 18, (d & 1) ? !(sgn_fwd > 0.f) : (sgn_fwd > 0.f), w.hi > 0.f,
+                       d >> 1, (d & 1) != 0);
+      }
+    } else {
 #define HOP(D, MU, BWD)                                                                                  \
     {                                                                                                    \
       R v[24], w;                                                                                        \
       load_hop<P>(inb, inn, nitems, ((long long)snb[(D) * S + sl] << lg) + col, v, w);                   \
       hop_any<R, BWD, MU>(acc, v, su + ((D) * S + sl) * 18, BWD ? sb : sf, w);                            \
     }
-    HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
-    HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
+      HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
+      HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
 #undef HOP
+    }
     hop_finish<R>(acc);
     red = epilogue<P, EPI, R>(acc, ep.e[l], L, nitems, j, col, aux, out, cr, cy, cp, alpha);
   }
@@ -307,6 +318,18 @@ __global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : 1) 
     R acc[24];
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] = 0;
+    if constexpr (std::is_same<R, dfloat>::value) {
+#pragma unroll 1
+      for (int d = 0; d < 8; ++d) {
+        bool crosses;
+        const int nb = neighbour(L, x, y, z, t, d, crosses);
+        R v[24], u[18], w;
+        load_hop<P>(inb, inn, nitems, ((long long)nb << L.lognpad) + col, v, w);
+        GIO<G>::load(gb, L.Vh, (d & 1) ? q : p, d >> 1, (d & 1) ? nb : i, u);
+        const bool wpos = !(crosses && L.tbc < 0.0);
+        hop_term_df_rt(acc, v, u, (d & 1) ? !(sgn_fwd > 0.f) : (sgn_fwd > 0.f), wpos, d >> 1, (d & 1) != 0);
+      }
+    } else {
 #define HOP(D, MU, BWD)                                                                  \
     {                                                                                    \
       bool crosses;                                                                      \
@@ -317,9 +340,10 @@ __global__ void __launch_bounds__(256, (P == P64 || P == PDF) ? DL_MINB_HI : 1) 
       if (crosses) w *= (R)L.tbc;                                                        \
       hop_any<R, BWD, MU>(acc, v, u, BWD ? sb : sf, w);                                   \
     }
-    HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
-    HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
+      HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
+      HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
 #undef HOP
+    }
     hop_finish<R>(acc);
     red = epilogue<P, EPI, R>(acc, ep.e[l], L, nitems, j, col, aux, out, cr, cy, cp, alpha);
   }

@@ -571,6 +571,81 @@ __device__ __forceinline__ void hop_term_df(dfloat acc[24], const dfloat v[24], 
   }
 }
 
+// The double-float hop with the direction and dagger as runtime values: the stencil
+// loops over its eight hops without unrolling, so one copy of this (long) body serves
+// all of them and the kernel's code fits the instruction cache (unrolled, the eight
+// specialised bodies made instruction fetch the kernel's main stall).
+// (G d)_sp = c_sp d_{src_sp} with c in {+-1, +-i}; (G^+ chi)_{2,3} likewise from chi_{0,1}.
+__device__ __forceinline__ dfloat df_sel(bool neg, const dfloat& x) { return neg ? -x : x; }
+// c z for c = (imag ? i : 1) * (neg ? -1 : 1):  (re, im) of the product
+__device__ __forceinline__ void df_cmul_unit(bool imag, bool neg, const dfloat& zr, const dfloat& zi, dfloat& re,
+                                             dfloat& im) {
+  re = imag ? df_sel(!neg, zi) : df_sel(neg, zr);  // i z = (-zi, zr)
+  im = imag ? df_sel(neg, zr) : df_sel(neg, zi);
+}
+__device__ __forceinline__ void hop_term_df_rt(dfloat acc[24], const dfloat v[24], const dfloat u[18], bool spos, bool wpos, int mu,
+                               bool dagu) {
+  // projection coefficients (G d)_sp = c d_src: mu 0: (-i d3, -i d2); 1: (-d3, d2); 2: (-i d2, i d3); 3: (d2, d3)
+  const bool pim = (mu == 0 || mu == 2);
+  const int src0 = (mu == 0 || mu == 1) ? 3 : 2, src1 = 5 - src0;
+  const bool neg0 = mu != 3, neg1 = mu == 0;  // sign of c for sp = 0, 1 (before the projector sign s)
+  dfloat hr[2][3], hi[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      const bool from3 = (sp ? src1 : src0) == 3;  // selects, not a runtime index (keeps v in registers)
+      const dfloat dr = from3 ? v[18 + 2 * c] : v[12 + 2 * c], di = from3 ? v[19 + 2 * c] : v[13 + 2 * c];
+      const bool ng = (sp ? neg1 : neg0) != !spos;  // times the projector sign s
+      dfloat gr, gi;
+      df_cmul_unit(pim, ng, dr, di, gr, gi);
+      hr[sp][c] = df_add_lazy(v[6 * sp + 2 * c], gr);
+      hi[sp][c] = df_add_lazy(v[6 * sp + 2 * c + 1], gi);
+    }
+  }
+  // G^+ chi: lower spin 2 from upper spin lsrc2 times c2, lower 3 from lsrc3 times c3:
+  // mu 0: (i c1, i c0); 1: (c1, -c0); 2: (i c0, -i c1); 3: (c0, c1)
+  const int lsrc2 = (mu == 0 || mu == 1) ? 1 : 0;
+  const bool lneg2 = false, lneg3 = (mu == 1 || mu == 2);
+  const bool sw = spos == wpos;  // sign of s w
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      dfloat cr, ci;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const dfloat ur = dagu ? u[2 * (3 * b + a)] : u[2 * (3 * a + b)];
+        const dfloat ui = dagu ? -u[2 * (3 * b + a) + 1] : u[2 * (3 * a + b) + 1];
+        if (b == 0) {
+          cr = df_mul_lazy(ur, hr[sp][b]);
+          ci = df_mul_lazy(ur, hi[sp][b]);
+        } else {
+          df_acc_mul(cr, ur, hr[sp][b]);
+          df_acc_mul(ci, ur, hi[sp][b]);
+        }
+        df_acc_mul(cr, -ui, hi[sp][b]);
+        df_acc_mul(ci, ui, hr[sp][b]);
+      }
+      cr = df_normalize(cr);
+      ci = df_normalize(ci);
+      df_acc(acc[6 * sp + 2 * a], df_sel(!wpos, cr));
+      df_acc(acc[6 * sp + 2 * a + 1], df_sel(!wpos, ci));
+      const bool to2 = sp == lsrc2;  // lower spin 2 or 3 (a uniform branch, constant indices)
+      const bool ln = (to2 ? lneg2 : lneg3) != !sw;
+      dfloat tr, ti;
+      df_cmul_unit(pim, ln, cr, ci, tr, ti);
+      if (to2) {
+        df_acc(acc[12 + 2 * a], tr);
+        df_acc(acc[13 + 2 * a], ti);
+      } else {
+        df_acc(acc[18 + 2 * a], tr);
+        df_acc(acc[19 + 2 * a], ti);
+      }
+    }
+  }
+}
+
 // The hop of the staged and direct stencils for every arithmetic type.
 template <typename R, bool DAGU, int mu>
 __device__ __forceinline__ void hop_any(R acc[24], const R v[24], const R u[18], R s, R w) {
