@@ -591,11 +591,11 @@ def learned_case(args):
     def progress(what):
         print(f"[learned {time.perf_counter() - t_start:8.1f} s] {what}", file=sys.stderr, flush=True)
     # training pairs from the plain solver (complex64 storage, FP64-accurate solutions); the
-    # residual loss needs the noise only
+    # residual loss uses the noise of the pairs only
     residual = args.nn_loss == "residual"
     out["loss"] = args.nn_loss
     eta = torch.empty((args.pairs, V * 12), dtype=torch.complex64, device="cuda")
-    sol = None if residual else torch.empty_like(eta)
+    sol = torch.empty_like(eta)
     hp = dl.dl_solve_params(tol=1e-10, max_iter=100000, prec_hi=dl.DL_F64, prec_lo=dl.DL_F32, delta=0.01, flavour=1,
                             chunk=0)
     torch.cuda.synchronize()
@@ -603,11 +603,10 @@ def learned_case(args):
     for b in range(0, args.pairs, 32):
         n = min(32, args.pairs - b)
         dl.dl_noise_z4(ctx, 2000 + cfg["id"], b, n, eta[b:b + n], dl.DL_C64)
-        if not residual:
-            dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
+        dl.dl_solve(ctx, eta[b:b + n], sol[b:b + n], n, dl.DL_C64, hp)
     torch.cuda.synchronize()
     out["seconds_pairs"] = time.perf_counter() - t0
-    progress(f"{args.pairs} training sources" + ("" if residual else " with solutions"))
+    progress(f"{args.pairs} training pairs")
     nn = dl.dl_nn_create(ctx, 4, 16, dl.DL_BF16)
     dl.dl_nn_set_weights(nn, synth.network_weights(4, 16, 3000 + cfg["id"]))
     tp = dl.dl_nn_train_params(steps=args.train_steps, batch=args.batch, lr=args.lr, beta1=0.9, beta2=0.999, eps=1e-8,

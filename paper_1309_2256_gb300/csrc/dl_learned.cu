@@ -487,7 +487,7 @@ dl_status dl_nn_train(dl_nn* nn, const dl_nn_train_params* prm, int n_pairs, con
                       double* loss_hist) try {
   if (!valid_nn(nn)) return DL_ERR_ARG;
   dl_ctx* c = nn->c;
-  if (!prm || !eta || !s || n_pairs < 1 || prm->steps < 0 || prm->batch < 1 || prm->batch > n_pairs ||
+  if (!prm || !eta || n_pairs < 1 || prm->steps < 0 || prm->batch < 1 || prm->batch > n_pairs ||
       !(prm->lr > 0.0) || !(prm->beta1 >= 0.0 && prm->beta1 < 1.0) || !(prm->beta2 >= 0.0 && prm->beta2 < 1.0) ||
       !(prm->eps > 0.0) || (dtype != DL_C128 && dtype != DL_C64) || (prm->loss != 0 && prm->loss != 1) ||
       (prm->loss == 0 && !s))
