@@ -580,7 +580,17 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     }
     if (!need) continue;
     std::vector<double> rr;
-    if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) return s;
+    if (prm.delta <= 0.0 && !final_check) {
+      // no reliable updates and no final check (the TSM's truncated LP solves): a column that
+      // stops only needs x += y; its true residual would decide nothing, so the normal
+      // operator is not applied and the iterated residual stands for it
+      CK(cudaMemcpyAsync(c->upd, mask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+      CK(dl::accum(B, hi, lo, x->ref(), F.y->ref(), c->upd, 1, c->st));
+      rr.assign(n, 0.0);
+      for (int i = 0; i < n; ++i) rr[i] = h.S[DL_S_RR * DL_NCMAX + i];
+    } else if ((s = reliable_update(c, B, hi, lo, f, F, x, b, mask, rr)) != DL_OK) {
+      return s;
+    }
     CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
     // 16-bit search directions lose conjugacy over several decades: every reliable
     // update restarts them from the true residual (p = r); FP32 ones are kept
