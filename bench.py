@@ -343,7 +343,9 @@ def plain_fp64_batched(dl, device, links):
 # current kernels on the 24^3 x 24, 16-column case; a launch's traffic is taken as
 # linear in its site-columns (links are read once per launch, every spinor stream once).
 # Classes without a capture of the current kernel report no traffic.
-NCU_DRAM_BYTES_PER_ITEM = {}
+#   16-bit CG update (dslash_pair<2, 3, 3, 1>): 736749568 + 251834880 bytes over
+#   24^4 / 2 sites x 16 columns (the algorithmic bytes are 997.9 MB)
+NCU_DRAM_BYTES_PER_ITEM = {("16-bit", "cg-update"): (736749568 + 251834880) / (24 ** 4 // 2 * 16)}
 
 LINK_BYTES = {"double-float": 144, "f32": 48, "16-bit": 24, "ieee-f64": 144}
 SPINOR_BYTES = {"double-float": 192, "f32": 96, "16-bit": 52, "ieee-f64": 192}

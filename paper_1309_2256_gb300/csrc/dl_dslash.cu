@@ -225,7 +225,10 @@ __device__ __forceinline__ void epilogue_pair(float2 acc[24], const Epi& e, cons
   if (!w1) red.y = 0.f;
 }
 
-template <int P, int G, int EPI>
+// SG = 0: the projector sign sgn_fwd is read at run time; SG = +-1 (16-bit storage): it is
+// sgn_fwd fixed at compile time, and the spin projection runs on the biased 16-bit values
+// (project_biased_pair).
+template <int P, int G, int EPI, int SG>
 __global__ void __launch_bounds__(128, DL_MINB_PAIR) dslash_pair(Batch B, int out_parity, float sgn_fwd, FieldRef in,
                                                                  FieldRef aux, FieldRef out,
                                                                  const void* __restrict__ gbase, EpiSet ep,
@@ -276,11 +279,20 @@ __global__ void __launch_bounds__(128, DL_MINB_PAIR) dslash_pair(Batch B, int ou
     float2 acc[24];
 #pragma unroll
     for (int m = 0; m < 24; ++m) acc[m] = make_float2(0.f, 0.f);
-#define HOP(D, MU, BWD)                                                                   \
-    {                                                                                     \
-      float2 v[24], w;                                                                    \
-      PIO<P>::load(inb, inn, nitems, ((long long)snb[(D) * S + sl] << lg) + col0, v, w);  \
-      hop_pair<MU, BWD>(acc, v, su + ((D) * S + sl) * 9, BWD ? sb : sf, w);               \
+#define HOP(D, MU, BWD)                                                                     \
+    {                                                                                       \
+      float2 v[24], w, hr[2][3], hi[2][3];                                                  \
+      const long long jn = ((long long)snb[(D) * S + sl] << lg) + col0;                     \
+      if constexpr (SG != 0) {                                                              \
+        constexpr int SH = BWD ? -SG : SG;                                                  \
+        PIO<P>::load_biased(inb, inn, nitems, jn, v, w);                                    \
+        project_biased_pair<MU, SH>(v, hr, hi);                                             \
+        apply_pair<MU, BWD>(acc, hr, hi, su + ((D) * S + sl) * 9, dup2((float)SH), w);     \
+      } else {                                                                              \
+        PIO<P>::load(inb, inn, nitems, jn, v, w);                                           \
+        project_pair<MU>(v, BWD ? sb : sf, hr, hi);                                         \
+        apply_pair<MU, BWD>(acc, hr, hi, su + ((D) * S + sl) * 9, BWD ? sb : sf, w);        \
+      }                                                                                     \
     }
     HOP(0, 0, false) HOP(1, 0, true) HOP(2, 1, false) HOP(3, 1, true)
     HOP(4, 2, false) HOP(5, 2, true) HOP(6, 3, false) HOP(7, 3, true)
@@ -369,6 +381,16 @@ cudaError_t ensure_smem_attr(K kernel, int bytes) {
 
 inline bool aligned32(const FieldRef& f) { return ((uintptr_t)f.data & 31) == 0 && ((uintptr_t)f.norm & 7) == 0; }
 
+template <int P, int G, int EPI, int SG>
+cudaError_t launch_pair(const Batch& B, int grid, size_t smem, float sgn, int op, FieldRef in, FieldRef aux, FieldRef out,
+                        const void* g, const EpiSet& ep, const int* active, double* partial, FieldRef cr, FieldRef cy,
+                        FieldRef cp, const double* alpha, cudaStream_t st) {
+  DL_CUDA_TRY(ensure_smem_attr(dslash_pair<P, G, EPI, SG>, 8 * 64 * 9 * 16 + 8 * 64 * 4));
+  DL_COUNT();
+  dslash_pair<P, G, EPI, SG><<<grid, 128, smem, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
+  return cudaGetLastError();
+}
+
 template <int P, int G, int EPI>
 cudaError_t launch_epi(const Batch& B, int grid, float sgn, int op, FieldRef in, FieldRef aux, FieldRef out,
                        const void* g, const EpiSet& ep, const int* active, double* partial, FieldRef cr, FieldRef cy,
@@ -387,10 +409,13 @@ cudaError_t launch_epi(const Batch& B, int grid, float sgn, int op, FieldRef in,
         return cudaErrorMisalignedAddress;
       const int S = 256 >> minlg;
       const size_t smem = (size_t)8 * S * 9 * sizeof(float4) + (size_t)8 * S * sizeof(int);
-      DL_CUDA_TRY(ensure_smem_attr(dslash_pair<P, G, EPI>, 8 * 64 * 9 * 16 + 8 * 64 * 4));
-      DL_COUNT();
-      dslash_pair<P, G, EPI><<<grid, 128, smem, st>>>(B, op, sgn, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha);
-      return cudaGetLastError();
+      if constexpr (P == P16) {
+        if (sgn > 0.f)
+          return launch_pair<P, G, EPI, 1>(B, grid, smem, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
+        return launch_pair<P, G, EPI, -1>(B, grid, smem, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
+      } else {
+        return launch_pair<P, G, EPI, 0>(B, grid, smem, sgn, op, in, aux, out, g, ep, active, partial, cr, cy, cp, alpha, st);
+      }
     }
   }
   if (minlg >= 2) {

@@ -110,6 +110,24 @@ template <> struct PIO<P16> {
       }
     }
   }
+  // v = the biased values 2^23 + 32768 + q (one byte permute each, no subtraction), for
+  // project_biased_pair; w as in load
+  __device__ static __forceinline__ void load_biased(const void* b, const float* nrm, long long st, long long j0,
+                                                     float2 v[24], float2& w) {
+    const uint4* p = (const uint4*)b;
+    const float2 nn = __ldg((const float2*)(nrm + j0));
+    w = mul2(nn, dup2(1.0f / 32767.0f));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unsigned a[8];
+      ld256(p + k * st + j0, a);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[8 * k + 2 * q] = make_float2(u16lo_biased(a[q]), u16lo_biased(a[4 + q]));
+        v[8 * k + 2 * q + 1] = make_float2(u16hi_biased(a[q]), u16hi_biased(a[4 + q]));
+      }
+    }
+  }
   __device__ static __forceinline__ void load_values(const void* b, const float* nrm, long long st, long long j0,
                                                      float2 v[24]) {
     float2 w;
@@ -163,11 +181,11 @@ template <> struct PIO<P16> {
 // basis (1 + s gamma_mu) maps the lower spins onto the upper ones through the block
 // G_mu (G_k = -i sigma_k, G_t = 1):  h = v_up + s G v_dn, chi = U' h,
 // acc_up += w chi, acc_dn += s w G^dagger chi.
-template <int MU, bool BWD>
-__device__ __forceinline__ void hop_pair(float2 acc[24], const float2 v[24], const float4* __restrict__ u, float2 s2,
-                                         float2 w2) {
+//
+// project_pair forms h for a run-time sign s; apply_pair does the rest.
+template <int MU>
+__device__ __forceinline__ void project_pair(const float2 v[24], float2 s2, float2 hr[2][3], float2 hi[2][3]) {
   const float2 ns2 = neg2(s2);
-  float2 hr[2][3], hi[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float2 u0r = v[2 * c], u0i = v[2 * c + 1], u1r = v[6 + 2 * c], u1i = v[7 + 2 * c];
@@ -186,6 +204,43 @@ __device__ __forceinline__ void hop_pair(float2 acc[24], const float2 v[24], con
       hr[1][c] = fma2(s2, d3r, u1r); hi[1][c] = fma2(s2, d3i, u1i);
     }
   }
+}
+
+// The same projection on 16-bit offset-binary values held as B + q, B = 2^23 + 32768
+// (PIO<P16>::load_biased), for a sign S known at compile time: every entry of h is an
+// integer q_u + q_d or q_u - q_d.  A difference of two biased values is one exact
+// subtraction (both lie in [2^23, 2^24)); a sum first takes 2B from one operand (q_u - B,
+// an integer below 2^24 in magnitude, exact) and then adds the other (the exact sum is a
+// small integer).  So h is bit-identical to project_pair on the decoded integers, with
+// one or two instructions per entry instead of three.
+template <int MU, int S>
+__device__ __forceinline__ void project_biased_pair(const float2 v[24], float2 hr[2][3], float2 hi[2][3]) {
+  const float2 m2b = dup2(-2.0f * DL_Q_BIAS), mone = dup2(-1.0f);
+#define DL_PM(U, D, SIG) ((SIG) > 0 ? add2(add2((U), m2b), (D)) : fma2(mone, (D), (U)))
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 u0r = v[2 * c], u0i = v[2 * c + 1], u1r = v[6 + 2 * c], u1i = v[7 + 2 * c];
+    const float2 d2r = v[12 + 2 * c], d2i = v[13 + 2 * c], d3r = v[18 + 2 * c], d3i = v[19 + 2 * c];
+    if (MU == 0) {
+      hr[0][c] = DL_PM(u0r, d3i, S); hi[0][c] = DL_PM(u0i, d3r, -S);
+      hr[1][c] = DL_PM(u1r, d2i, S); hi[1][c] = DL_PM(u1i, d2r, -S);
+    } else if (MU == 1) {
+      hr[0][c] = DL_PM(u0r, d3r, -S); hi[0][c] = DL_PM(u0i, d3i, -S);
+      hr[1][c] = DL_PM(u1r, d2r, S); hi[1][c] = DL_PM(u1i, d2i, S);
+    } else if (MU == 2) {
+      hr[0][c] = DL_PM(u0r, d2i, S); hi[0][c] = DL_PM(u0i, d2r, -S);
+      hr[1][c] = DL_PM(u1r, d3i, -S); hi[1][c] = DL_PM(u1i, d3r, S);
+    } else {
+      hr[0][c] = DL_PM(u0r, d2r, S); hi[0][c] = DL_PM(u0i, d2i, S);
+      hr[1][c] = DL_PM(u1r, d3r, S); hi[1][c] = DL_PM(u1i, d3i, S);
+    }
+  }
+#undef DL_PM
+}
+
+template <int MU, bool BWD>
+__device__ __forceinline__ void apply_pair(float2 acc[24], const float2 hr[2][3], const float2 hi[2][3],
+                                           const float4* __restrict__ u, float2 s2, float2 w2) {
   // chi = U' h: (ur + i ui)(hr + i hi) = (ur hr - ui hi) + i (ur hi + ui hr); for
   // U^dagger the entry is conj(U_ba): ui changes sign
   float2 cr[2][3], ci[2][3];

@@ -64,6 +64,10 @@ def test_roofline_picks_the_class_with_the_most_time_per_sweep():
     assert r["frac"] == pytest.approx(r["achieved"] / peaks["hbm_gbs"], rel=1e-3)
     assert rows[1]["bytes_per_launch"] == 4 * V * 144 + 2 * Vh * 16 * 192
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    # traffic: the ncu bytes per site-column of the class, times the launch's site-columns
+    per_item = bench.NCU_DRAM_BYTES_PER_ITEM[("16-bit", "cg-update")]
+    assert r["traffic"] == int(per_item * Vh * 16)
+    assert 0.9 < r["traffic"] / expect < 1.1
 
 
 def test_gamma_matrices_of_the_error_report():
