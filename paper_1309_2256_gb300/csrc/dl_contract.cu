@@ -11,6 +11,7 @@
 // (1 + exp(-i p_mu)) for spatial mu and a sum of neighbouring time slices for t.
 #include "dl_internal.cuh"
 #include "dl_kernels.h"
+#include "dl_pair.cuh"
 
 namespace {
 
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
   typedef RPair<R> cr;
   cr* cs = (cr*)smem_raw;                        // [16][X][cw] site components
   cr* pht = cs + 16 * L.X * cw;                  // [NX][X] phases
-  cr* part = pht + NX * L.X;                     // [2 halves][16][NX][cw] partial DFT sums
+  cr* part = pht + NX * L.X;                     // [4 or 2 parts][16][NX][cw] partial DFT sums
   const int row = blockIdx.x;                    // (k * Z + z) * Y + y for slice t = t0 + k dt
   const int y = row % L.Y, z = (row / L.Y) % L.Z, t = S.t0 + S.dt * (row / (L.Y * L.Z));
   const int x = threadIdx.x >> cwlog, cl = threadIdx.x & (cw - 1);
@@ -316,39 +317,104 @@ __global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, 
       cs[(k * L.X + x) * cw + cl].y = cim[k];
     }
     __syncthreads();
-    // x DFT, register-blocked: task (half of the row, component k, column cc) reads each
-    // site value once and updates all NX momenta; the two halves are added in a fixed order
-    const int half = (L.X + 1) >> 1;
-    for (int task = threadIdx.x; task < 32 * cw; task += blockDim.x) {
-      const int cc = task & (cw - 1);
-      const int k = (task >> cwlog) & 15;
-      const int xh = task >> (cwlog + 4);
-      const int x0 = xh * half, x1 = (x0 + half < L.X) ? x0 + half : L.X;
-      constexpr int NXC = MXT >= 0 ? 2 * MXT + 1 : DL_NXMAX;
-      R ar[NXC], ai[NXC];
+    // x DFT, register-blocked and paired in +-p_x.  The phases of the momenta +m and -m
+    // are c -+ i s with the same c = cos(2 pi m x / X) and s = sin(2 pi m x / X), so with
+    // Pc = sum_x v c and Q = sum_x v (-s)
+    //   out(+m) = (Pc.re - Q.im, Pc.im + Q.re),   out(-m) = (Pc.re + Q.im, Pc.im - Q.re):
+    // four multiply-adds per site for both momenta (eight for two plain DFT terms).  A task
+    // (part of the row, component k, column or column pair) reads each site value once;
+    // the parts are added in a fixed order.  FP32 runs two columns per task in packed
+    // FP32x2 arithmetic over four parts of the row, the other types one column over two.
+    constexpr int MC = MXT >= 0 ? MXT : (DL_NXMAX - 1) / 2;
+    int nq = 2;
+    bool packed = false;
+    if constexpr (std::is_same<R, float>::value) packed = cw >= 2;
+    if constexpr (std::is_same<R, float>::value) {
+      if (packed) {
+        nq = 4;
+        const int hp = cw >> 1, qlen = (L.X + 3) >> 2;
+        for (int task = threadIdx.x; task < 64 * hp; task += blockDim.x) {
+          const int cp = task % hp, k = (task / hp) & 15, q = task / (16 * hp);
+          const int x0 = q * qlen, x1 = (x0 + qlen < L.X) ? x0 + qlen : L.X;
+          float2 p0r = make_float2(0.f, 0.f), p0i = p0r, pcr[MC + 1], pci[MC + 1], qr[MC + 1], qi[MC + 1];
 #pragma unroll
-      for (int kx = 0; kx < NXC; ++kx) ar[kx] = ai[kx] = 0;
-      for (int xx = x0; xx < x1; ++xx) {
-        const cr v = cs[(k * L.X + xx) * cw + cc];
+          for (int m = 0; m <= MC; ++m) pcr[m] = pci[m] = qr[m] = qi[m] = p0r;
+          for (int xx = x0; xx < x1; ++xx) {
+            const float4 v = *(const float4*)&cs[(k * L.X + xx) * cw + 2 * cp];
+            const float2 vr = make_float2(v.x, v.z), vi = make_float2(v.y, v.w);
+            p0r = add2(p0r, vr);
+            p0i = add2(p0i, vi);
 #pragma unroll
-        for (int kx = 0; kx < NXC; ++kx)
-          if (MXT >= 0 || kx < NX) {
-            const cr w = pht[kx * L.X + xx];
-            ar[kx] += v.x * w.x - v.y * w.y;
-            ai[kx] += v.x * w.y + v.y * w.x;
+            for (int m = 1; m <= MC; ++m)
+              if (MXT >= 0 || m <= mx) {
+                const cr w = pht[(mx + m) * L.X + xx];
+                const float2 c2 = dup2(w.x), s2 = dup2(w.y);
+                pcr[m] = fma2(vr, c2, pcr[m]);
+                pci[m] = fma2(vi, c2, pci[m]);
+                qr[m] = fma2(vr, s2, qr[m]);
+                qi[m] = fma2(vi, s2, qi[m]);
+              }
+          }
+          cr* dst = part + (size_t)(q * 16 + k) * NX * cw + 2 * cp;
+          dst[mx * cw] = cr{p0r.x, p0i.x};
+          dst[mx * cw + 1] = cr{p0r.y, p0i.y};
+#pragma unroll
+          for (int m = 1; m <= MC; ++m)
+            if (MXT >= 0 || m <= mx) {
+              dst[(mx + m) * cw] = cr{pcr[m].x - qi[m].x, pci[m].x + qr[m].x};
+              dst[(mx + m) * cw + 1] = cr{pcr[m].y - qi[m].y, pci[m].y + qr[m].y};
+              dst[(mx - m) * cw] = cr{pcr[m].x + qi[m].x, pci[m].x - qr[m].x};
+              dst[(mx - m) * cw + 1] = cr{pcr[m].y + qi[m].y, pci[m].y - qr[m].y};
+            }
+        }
+      }
+    }
+    if (!packed) {
+      const int qlen = (L.X + 1) >> 1;
+      for (int task = threadIdx.x; task < 32 * cw; task += blockDim.x) {
+        const int cc = task & (cw - 1);
+        const int k = (task >> cwlog) & 15;
+        const int q = task >> (cwlog + 4);
+        const int x0 = q * qlen, x1 = (x0 + qlen < L.X) ? x0 + qlen : L.X;
+        R p0r = 0, p0i = 0, pcr[MC + 1], pci[MC + 1], qr[MC + 1], qi[MC + 1];
+#pragma unroll
+        for (int m = 0; m <= MC; ++m) pcr[m] = pci[m] = qr[m] = qi[m] = 0;
+        for (int xx = x0; xx < x1; ++xx) {
+          const cr v = cs[(k * L.X + xx) * cw + cc];
+          p0r += v.x;
+          p0i += v.y;
+#pragma unroll
+          for (int m = 1; m <= MC; ++m)
+            if (MXT >= 0 || m <= mx) {
+              const cr w = pht[(mx + m) * L.X + xx];
+              pcr[m] += v.x * w.x;
+              pci[m] += v.y * w.x;
+              qr[m] += v.x * w.y;
+              qi[m] += v.y * w.y;
+            }
+        }
+        cr* dst = part + (size_t)(q * 16 + k) * NX * cw + cc;
+        dst[mx * cw] = cr{p0r, p0i};
+#pragma unroll
+        for (int m = 1; m <= MC; ++m)
+          if (MXT >= 0 || m <= mx) {
+            dst[(mx + m) * cw] = cr{pcr[m] - qi[m], pci[m] + qr[m]};
+            dst[(mx - m) * cw] = cr{pcr[m] + qi[m], pci[m] - qr[m]};
           }
       }
-#pragma unroll
-      for (int kx = 0; kx < NXC; ++kx)
-        if (MXT >= 0 || kx < NX) part[((xh * 16 + k) * NX + kx) * cw + cc] = cr{ar[kx], ai[kx]};
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 16 * NX * cw; e += blockDim.x) {
       const int cc = e & (cw - 1);
       const int kx = (e >> cwlog) % NX;
       const int k = (e >> cwlog) / NX;
-      const cr a = part[(k * NX + kx) * cw + cc], b = part[((16 + k) * NX + kx) * cw + cc];
-      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] = cr{a.x + b.x, a.y + b.y};
+      cr a = part[(k * NX + kx) * cw + cc];
+      for (int q = 1; q < nq; ++q) {
+        const cr b = part[((q * 16 + k) * NX + kx) * cw + cc];
+        a.x += b.x;
+        a.y += b.y;
+      }
+      G1[(((long long)(16 * d + k) * nrows + row) * NX + kx) * npad + blockIdx.y * cw + cc] = a;
     }
   }
 }
@@ -387,24 +453,38 @@ __global__ void __launch_bounds__(256) dft_kernel(const RPair<R>* __restrict__ i
     if (ss < tw) slab[e] = src[(long long)j * stride + ss];
   }
   __syncthreads();
+  // the momenta +mm and -mm share c and s of their phases c -+ i s: with Pc = sum v c and
+  // Q = sum v (-s), out(+mm) = (Pc.re - Q.im, Pc.im + Q.re), out(-mm) = (Pc.re + Q.im, Pc.im - Q.re)
   const int nk = 2 * m + 1;
-  for (int o = threadIdx.x; o < nk * DL_DFT_TILE; o += blockDim.x) {
-    const int k = o / DL_DFT_TILE, ss = o % DL_DFT_TILE;
+  for (int o = threadIdx.x; o < (m + 1) * DL_DFT_TILE; o += blockDim.x) {
+    const int mm = o / DL_DFT_TILE, ss = o % DL_DFT_TILE;
     if (ss >= tw) continue;
-    int n = k - m;
-    n = ((n % len) + len) % len;
-    R re = 0, im = 0;
+    const int n = mm % len;
+    R pr = 0, pi = 0, qr = 0, qi = 0;
+    if (mm == 0) {
+#pragma unroll 4
+      for (int jx = 0; jx < len; ++jx) {
+        const cr v = slab[jx * DL_DFT_TILE + ss];
+        pr += v.x;
+        pi += v.y;
+      }
+      out[(b * nk + m) * stride + s0 + ss] = cr{pr, pi};
+      continue;
+    }
     int q = 0;
 #pragma unroll 4
     for (int jx = 0; jx < len; ++jx) {
       const cr v = slab[jx * DL_DFT_TILE + ss];
       const cr w = phs[q];
-      re += v.x * w.x - v.y * w.y;
-      im += v.x * w.y + v.y * w.x;
+      pr += v.x * w.x;
+      pi += v.y * w.x;
+      qr += v.x * w.y;
+      qi += v.y * w.y;
       q += n;
       if (q >= len) q -= len;
     }
-    out[(b * nk + k) * stride + s0 + ss] = cr{re, im};
+    out[(b * nk + m + mm) * stride + s0 + ss] = cr{pr - qi, pi + qr};
+    out[(b * nk + m - mm) * stride + s0 + ss] = cr{pr + qi, pi - qr};
   }
 }
 
@@ -649,7 +729,9 @@ cudaError_t launch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx,
                       cudaStream_t st) {
   const LatDesc& L = B.lat[0];
   const int NX = 2 * mx + 1;
-  const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 32 * NX * (1 << cwlog)) * 2 * sizeof(R);
+  // site components, phase table, partial x-DFT sums (four row parts for FP32, two otherwise)
+  const int nq = std::is_same<R, float>::value ? 4 : 2;
+  const size_t smem = (size_t)(16 * L.X * (1 << cwlog) + NX * L.X + 16 * nq * NX * (1 << cwlog)) * 2 * sizeof(R);
   if (smem > 200000) return cudaErrorInvalidValue;
   DL_COUNT();
   phase_table_kernel<R><<<(NX * L.X + 255) / 256, 256, 0, st>>>(L.X, mx, (RPair<R>*)phx);
@@ -661,7 +743,8 @@ cudaError_t launch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx,
 }
 
 // One (precision, estimator, derivative) combination: its arithmetic type and gauge
-// copy, and for the FP32 local contractions of the LP pipeline a kernel per x extent.
+// copy, and for the local contractions a kernel per x extent (FP32: mx <= 3; double-float:
+// mx = 3, the extent of |n|^2 <= 9).
 template <int PR, int MD, bool DV>
 cudaError_t dispatch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int mx, FieldRef s_e, FieldRef s_o,
                         FieldRef eta_e, FieldRef eta_o, const void* g64, const void* g32, int rec32, double2* phx,
@@ -670,6 +753,9 @@ cudaError_t dispatch_cx(const Batch& B, dim3 grid, int threads, int cwlog, int m
   if constexpr (PR == P64) {
     return launch_cx<PR, MD, DV, double, G64R18, -1>(ARGS, g64, phx, G1, S, st);
   } else if constexpr (PR == PDF) {
+    if constexpr (!DV) {
+      if (mx == 3) return launch_cx<PR, MD, DV, dfloat, GDF18, 3>(ARGS, g64, phx, G1, S, st);  // |n|^2 <= 9 .. 15
+    }
     return launch_cx<PR, MD, DV, dfloat, GDF18, -1>(ARGS, g64, phx, G1, S, st);
   } else {
     if constexpr (!DV) {
