@@ -82,6 +82,9 @@ cudaError_t nn_backward_w(const LatDesc& L, int prec, int grec, int parity, Fiel
 cudaError_t nn_wsum(const float2* partial, int nslice, size_t nW, float2* grad, cudaStream_t st);
 // tensor-core forward (bfloat16 activations): B chunks of a layer (36 x 2 KB), then the layer
 cudaError_t nn_tc_prep(const float2* W, int ci, int co, void* Bc, cudaStream_t st);
+// weights of the adjoint layer (C_out -> C_in channels, [9][4][ci][co]): with them the
+// forward kernels compute the input gradient
+cudaError_t nn_adj_weights(const float2* W, int ci, int co, float2* Wa, cudaStream_t st);
 cudaError_t nn_forward_tc(const LatDesc& L, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef y, const void* g32,
                           const void* Bc, int ci, int co, int lgin, int lgout, int* err, cudaStream_t st);
 cudaError_t nn_lossgrad(const Batch& B, int prec, FieldRef y, FieldRef s, FieldRef g, const double* inv_ns, double* partial,

@@ -23,10 +23,13 @@ struct dl_nn {
   int adam_t = 0;  // Adam steps taken
   double* dscal = nullptr;  // device scalars: [0, 2) dot products, [2, 2 + 2 * nloss) loss partial sums
   int nloss = 0;
-  // tensor-core forward (bfloat16 activations): per layer 36 B chunks of 2 KB laid out from W
+  // tensor-core layers (bfloat16 activations): per layer 36 B chunks of 2 KB laid out from W
+  // (tcB) and from the adjoint layer's weights (tcBa, for input gradients and N^+)
   bool use_tc = false;
   bool tc_dirty = true;     // W changed since the chunks were laid out
   void* tcB = nullptr;
+  void* tcBa = nullptr;
+  float2* Wa = nullptr;     // one layer's adjoint weights (scratch, 36 x 16 x 16 complex)
   int* tc_err = nullptr;    // set by the kernel when a bounded wait ran out
 };
 
@@ -66,16 +69,41 @@ dl_status get_acts(dl_nn* nn, const char* tag, int l0, Acts& A) {
 
 constexpr size_t TC_LAYER_BYTES = 36 * 2048;
 
+// Lay out the tensor-core B chunks of every layer and of its adjoint after W changed.
+dl_status tc_prepare(dl_nn* nn) {
+  dl_ctx* c = nn->c;
+  if (!nn->use_tc || !nn->tc_dirty) return DL_OK;
+  for (int l = 0; l < nn->nl; ++l) {
+    CK(dl::nn_tc_prep(nn->W + nn->woff[l], nn->ci[l], nn->co[l], (char*)nn->tcB + l * TC_LAYER_BYTES, c->st));
+    CK(dl::nn_adj_weights(nn->W + nn->woff[l], nn->ci[l], nn->co[l], nn->Wa, c->st));
+    CK(dl::nn_tc_prep(nn->Wa, nn->co[l], nn->ci[l], (char*)nn->tcBa + l * TC_LAYER_BYTES, c->st));
+  }
+  nn->tc_dirty = false;
+  return DL_OK;
+}
+
+// G[l] = layer_l^+ (G[l+1]), output parity p: the adjoint layer on the tensor cores
+// (bfloat16 activations, when enabled), else the input-gradient kernel on the CUDA cores.
+dl_status layer_adjoint(dl_nn* nn, const LatDesc& L, int l, int p, const Acts& G) {
+  dl_ctx* c = nn->c;
+  FieldRef out = p ? G.o[l]->ref() : G.e[l]->ref();
+  if (nn->use_tc)
+    CK(dl::nn_forward_tc(L, c->rec32, p, G.e[l + 1]->ref(), G.o[l + 1]->ref(), out, c->g32,
+                         (const char*)nn->tcBa + l * TC_LAYER_BYTES, nn->co[l], nn->ci[l], lg_out(nn, l), lg_in(nn, l),
+                         nn->tc_err, c->st));
+  else
+    CK(dl::nn_backward_x(L, nn->act, c->rec32, p, G.e[l + 1]->ref(), G.o[l + 1]->ref(), out, c->g32,
+                         nn->W + nn->woff[l], nn->ci[l], nn->co[l], lg_in(nn, l), lg_out(nn, l), c->st));
+  return DL_OK;
+}
+
 // X[l+1] = layer_l(X[l]) for every layer, both output parities: on the tensor cores
 // for bfloat16 activations (when enabled), else on the CUDA cores.
 dl_status forward(dl_nn* nn, const Acts& X) {
   dl_ctx* c = nn->c;
   const LatDesc L = make_batch(c, 1).lat[0];
-  if (nn->use_tc && nn->tc_dirty) {
-    for (int l = 0; l < nn->nl; ++l)
-      CK(dl::nn_tc_prep(nn->W + nn->woff[l], nn->ci[l], nn->co[l], (char*)nn->tcB + l * TC_LAYER_BYTES, c->st));
-    nn->tc_dirty = false;
-  }
+  dl_status st;
+  if ((st = tc_prepare(nn)) != DL_OK) return st;
   for (int l = 0; l < nn->nl; ++l)
     for (int p = 0; p < 2; ++p) {
       FieldRef out = p ? X.o[l + 1]->ref() : X.e[l + 1]->ref();
@@ -106,6 +134,8 @@ dl_status check_tc(dl_nn* nn) {
 dl_status backward(dl_nn* nn, const Acts& X, const Acts& G) {
   dl_ctx* c = nn->c;
   const LatDesc L = make_batch(c, 1).lat[0];
+  dl_status st;
+  if ((st = tc_prepare(nn)) != DL_OK) return st;
   for (int l = nn->nl - 1; l >= 0; --l) {
     for (int p = 0; p < 2; ++p)
       CK(dl::nn_backward_w(L, nn->act, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(),
@@ -113,22 +143,20 @@ dl_status backward(dl_nn* nn, const Acts& X, const Acts& G) {
                            lg_out(nn, l), nn->wpart + nn->poff[l], nn->slots, c->st));
     if (l > 0)
       for (int p = 0; p < 2; ++p)
-        CK(dl::nn_backward_x(L, nn->act, c->rec32, p, G.e[l + 1]->ref(), G.o[l + 1]->ref(),
-                             p ? G.o[l]->ref() : G.e[l]->ref(), c->g32, nn->W + nn->woff[l], nn->ci[l], nn->co[l],
-                             lg_in(nn, l), lg_out(nn, l), c->st));
+        if ((st = layer_adjoint(nn, L, l, p, G)) != DL_OK) return st;
   }
   return DL_OK;
 }
 
-// G[0] = N^+ G[nl]: the adjoint of every layer (the input-gradient kernels) from the last to the first.
+// G[0] = N^+ G[nl]: the adjoint of every layer from the last to the first.
 dl_status adjoint(dl_nn* nn, const Acts& G) {
   dl_ctx* c = nn->c;
   const LatDesc L = make_batch(c, 1).lat[0];
+  dl_status st;
+  if ((st = tc_prepare(nn)) != DL_OK) return st;
   for (int l = nn->nl - 1; l >= 0; --l)
     for (int p = 0; p < 2; ++p)
-      CK(dl::nn_backward_x(L, nn->act, c->rec32, p, G.e[l + 1]->ref(), G.o[l + 1]->ref(),
-                           p ? G.o[l]->ref() : G.e[l]->ref(), c->g32, nn->W + nn->woff[l], nn->ci[l], nn->co[l],
-                           lg_in(nn, l), lg_out(nn, l), c->st));
+      if ((st = layer_adjoint(nn, L, l, p, G)) != DL_OK) return st;
   return DL_OK;
 }
 
@@ -322,6 +350,8 @@ dl_status dl_nn_create(dl_ctx* c, int n_layers, int channels, int act_prec, dl_n
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->wpart, sizeof(float2) * nn->npart * nn->slots);
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->dscal, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&nn->tcB, TC_LAYER_BYTES * n_layers);
+  if (e == cudaSuccess) e = cudaMalloc(&nn->tcBa, TC_LAYER_BYTES * n_layers);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&nn->Wa, sizeof(float2) * 36 * 16 * 16);
   if (e == cudaSuccess) e = cudaMalloc((void**)&nn->tc_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(nn->tc_err, 0, sizeof(int));
   nn->use_tc = nn->act == PBF;  // bfloat16 activations run on the tensor cores by default
@@ -352,6 +382,8 @@ void dl_nn_destroy(dl_nn* nn) try {
   cudaFree(nn->wpart);
   cudaFree(nn->dscal);
   cudaFree(nn->tcB);
+  cudaFree(nn->tcBa);
+  cudaFree(nn->Wa);
   cudaFree(nn->tc_err);
   delete nn;
 } catch (...) {

@@ -509,6 +509,26 @@ __global__ void nn_tc_prep_kernel(const float2* __restrict__ W, int CI, int CO, 
   Bc[(size_t)chunk * 1024 + tc_off(n, k) / 2] = __float2bfloat16_rn(v);
 }
 
+// Weights of the adjoint layer, so that the tensor-core forward computes the input
+// gradient (the adjoint N^+ of a layer).  The layer sums W[t][b] H_b T_t x over terms t
+// (T_0 = 1, T_{1+2mu} = U_mu(x) x(x+mu), T_{2+2mu} = U_mu(x-mu)^+ x(x-mu)) and spin factors
+// H_b; the channel mixing, the spin factor and the colour transport act on different
+// indices and commute, and T_{1+2mu}^+ = T_{2+2mu}, so the adjoint is a layer of the same
+// form from C_out to C_in channels with
+//   Wa[t][b][i][o] = s_b conj(W[t'][b][o][i]),  t' = t with the two hops of each mu swapped,
+// s_b = -1 for H_3 = g5 g_mu (its adjoint is -g5 g_mu) and +1 otherwise (1, g5, g_mu are
+// Hermitian).  Wa is [9][4][CI][CO].
+__global__ void nn_adj_weights_kernel(const float2* __restrict__ W, int CI, int CO, float2* __restrict__ Wa) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 36 * CI * CO) return;
+  const int o = e % CO, i = (e / CO) % CI, tb = e / (CO * CI);
+  const int t = tb >> 2, b = tb & 3;
+  const int ts = t == 0 ? 0 : ((t & 1) ? t + 1 : t - 1);
+  const float2 w = W[((size_t)(4 * ts + b) * CO + o) * CI + i];
+  const float sg = (t != 0 && b == 3) ? -1.f : 1.f;
+  Wa[e] = make_float2(sg * w.x, -sg * w.y);
+}
+
 // 256 threads: thread tid transports channels 8 (tid >> 7) .. 8 (tid >> 7) + 7 of site
 // tid & 127; in the epilogue warps w and w + 4 share TMEM lanes 32 (w & 3) .. and
 // write output channels 0..7 and 8..15 of those sites.
@@ -805,6 +825,13 @@ cudaError_t nn_tc_prep(const float2* W, int ci, int co, void* Bc, cudaStream_t s
   if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
   DL_COUNT();
   nn_tc_prep_kernel<<<36 * 1024 / 256, 256, 0, st>>>(W, ci, co, (__nv_bfloat16*)Bc);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_adj_weights(const float2* W, int ci, int co, float2* Wa, cudaStream_t st) {
+  if (ci > 16 || co > 16 || ci < 1 || co < 1) return cudaErrorInvalidValue;
+  DL_COUNT();
+  nn_adj_weights_kernel<<<(36 * ci * co + 255) / 256, 256, 0, st>>>(W, ci, co, Wa);
   return cudaGetLastError();
 }
 

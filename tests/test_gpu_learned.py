@@ -117,6 +117,48 @@ def test_tensor_core_forward_matches_cuda_core_forward(dl):
         assert np.abs(outs[1][r] - outs[0][r]).max() <= 3e-2 * sc, r
 
 
+def test_tensor_core_adjoint_matches_oracle(dl):
+    """bfloat16 network, 16 channels on an 8^4 lattice: N^+ y on the tensor cores (the
+    adjoint layers as forward layers of conjugate-transposed, hop-swapped weights) against
+    the CUDA-core input-gradient kernels and the oracle's layer adjoints; and
+    <N x, y> = <x, N^+ y> within the bfloat16 rounding of both sides."""
+    dims = (8, 8, 8, 8)
+    n_layers, c = 4, 16
+    links = synth.gauge_links(dims, 0.4, 318)
+    w = synth.network_weights(n_layers, c, 66, scale=0.6, identity=0.5)
+    y = synth.gaussian_spinors(dims, 2, 67)
+    x = synth.gaussian_spinors(dims, 2, 68)
+    ctx = _ctx(dl, dims, links, 0.16, 0.01)
+    outs = {}
+    try:
+        nn = dl.dl_nn_create(ctx, n_layers, c, dl.DL_BF16)
+        dl.dl_nn_set_weights(nn, w)
+        for tc in (1, 0):
+            dl.dl_nn_set_tensor_cores(nn, tc)
+            out = torch.zeros(y.size, dtype=torch.complex128, device="cuda")
+            dl.dl_nn_apply_adjoint(nn, 2, _dev(y), out)
+            outs[tc] = out.cpu().numpy().reshape(y.shape)
+        dl.dl_nn_set_tensor_cores(nn, 1)
+        nx = torch.zeros(x.size, dtype=torch.complex128, device="cuda")
+        dl.dl_nn_apply(nn, 2, _dev(x), nx)
+        nx = nx.cpu().numpy().reshape(x.shape)
+        dl.dl_nn_destroy(nn)
+    finally:
+        dl.dl_destroy(ctx)
+    ws = _to_oracle(w, n_layers, c)
+    for r in range(2):
+        g = y[r:r + 1]
+        for li in range(n_layers - 1, -1, -1):
+            ci = 1 if li == 0 else c
+            x0 = np.zeros((ci,) + dims[::-1] + (4, 3), dtype=np.complex128)
+            _, g = network.layer_backward(links, ws[li], x0, g)
+        sc = np.abs(g).max()
+        assert np.abs(outs[1][r] - g[0]).max() <= 3e-2 * sc, r
+        assert np.abs(outs[1][r] - outs[0][r]).max() <= 3e-2 * sc, r
+        lhs, rhs = np.vdot(nx[r], y[r]), np.vdot(x[r], outs[1][r])
+        assert abs(lhs - rhs) <= 2e-2 * np.linalg.norm(nx[r]) * np.linalg.norm(y[r]), r
+
+
 def test_adjoint_matches_oracle(dl):
     """N^+ y from the input-gradient kernels against the oracle's layer adjoints (FP32)."""
     dims = (4, 4, 4, 4)
