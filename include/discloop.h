@@ -386,11 +386,12 @@ void dl_nn_destroy(dl_nn* nn);
 /* Complex weights over all layers (the length of the set/get arrays / 2 floats). */
 long long dl_nn_weight_count(const dl_nn* nn);
 /* Layers of bfloat16 networks: 1 (the default for DL_BF16 activations) runs the channel
- * mixing of the forward pass and of the adjoint (N^+, the input gradients of training) as
- * tcgen05 matrix products (bf16 operands from shared memory, FP32 accumulators in tensor
- * memory; the adjoint as a layer of the same form with conjugate-transposed weights and
- * the two hops of each direction swapped), 0 on the CUDA cores (FP32 FMA).  The weight
- * gradients always run on the CUDA cores.  DL_ERR_ARG for FP32 activations. */
+ * mixing of the forward pass, of the adjoint (N^+, the input gradients of training) and of
+ * the weight gradients as tcgen05 matrix products (bf16 operands from shared memory, FP32
+ * accumulators in tensor memory; the adjoint as a layer of the same form with
+ * conjugate-transposed weights and the two hops of each direction swapped; the weight
+ * gradients with the lattice sites as the reduction dimension), 0 on the CUDA cores (FP32
+ * FMA).  DL_ERR_ARG for FP32 activations. */
 dl_status dl_nn_set_tensor_cores(dl_nn* nn, int enable);
 dl_status dl_nn_set_weights(dl_nn* nn, const float* host_w);   /* host complex64 */
 dl_status dl_nn_get_weights(dl_nn* nn, float* host_w);

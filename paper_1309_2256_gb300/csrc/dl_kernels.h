@@ -79,6 +79,11 @@ cudaError_t nn_backward_x(const LatDesc& L, int prec, int grec, int parity, Fiel
 cudaError_t nn_backward_w(const LatDesc& L, int prec, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef gp,
                           const void* g32, int ci, int co, int lgin, int lgout, float2* partial, int slots,
                           cudaStream_t st);
+// the same weight-gradient partials on the tensor cores (bfloat16 activations; `slots` persistent
+// CTAs, at most one per 32-site tile); err is set when a bounded wait ran out
+cudaError_t nn_backward_w_tc(const LatDesc& L, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef gp,
+                             const void* g32, int ci, int co, int lgin, int lgout, float2* partial, int slots, int* err,
+                             cudaStream_t st);
 cudaError_t nn_wsum(const float2* partial, int nslice, size_t nW, float2* grad, cudaStream_t st);
 // tensor-core forward (bfloat16 activations): B chunks of a layer (36 x 2 KB), then the layer
 cudaError_t nn_tc_prep(const float2* W, int ci, int co, void* Bc, cudaStream_t st);

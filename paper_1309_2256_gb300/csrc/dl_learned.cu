@@ -137,10 +137,15 @@ dl_status backward(dl_nn* nn, const Acts& X, const Acts& G) {
   dl_status st;
   if ((st = tc_prepare(nn)) != DL_OK) return st;
   for (int l = nn->nl - 1; l >= 0; --l) {
-    for (int p = 0; p < 2; ++p)
-      CK(dl::nn_backward_w(L, nn->act, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(),
-                           p ? G.o[l + 1]->ref() : G.e[l + 1]->ref(), c->g32, nn->ci[l], nn->co[l], lg_in(nn, l),
-                           lg_out(nn, l), nn->wpart + nn->poff[l], nn->slots, c->st));
+    for (int p = 0; p < 2; ++p) {
+      FieldRef gp = p ? G.o[l + 1]->ref() : G.e[l + 1]->ref();
+      if (nn->use_tc)
+        CK(dl::nn_backward_w_tc(L, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(), gp, c->g32, nn->ci[l], nn->co[l],
+                                lg_in(nn, l), lg_out(nn, l), nn->wpart + nn->poff[l], nn->slots, nn->tc_err, c->st));
+      else
+        CK(dl::nn_backward_w(L, nn->act, c->rec32, p, X.e[l]->ref(), X.o[l]->ref(), gp, c->g32, nn->ci[l], nn->co[l],
+                             lg_in(nn, l), lg_out(nn, l), nn->wpart + nn->poff[l], nn->slots, c->st));
+    }
     if (l > 0)
       for (int p = 0; p < 2; ++p)
         if ((st = layer_adjoint(nn, L, l, p, G)) != DL_OK) return st;

@@ -716,6 +716,217 @@ __global__ void __launch_bounds__(256, 1) nn_fwd_tc_kernel(LatDesc L, int p, Fie
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ------------------------------------------- weight gradient on the tensor cores
+// bfloat16 activations.  With F_(t,i,kind)(site, h, c6) the transported inputs of the
+// forward pass (kind 0: Z = T_t x_i, kind 1: g_mu Z; spin half h, spin-colour component c6
+// of that half) and G(site, h, c6)[o] the output gradient, the gradient of the weight
+// combination C_(h,t,kind)[o][i] of the forward kernel is
+//   dC_h[o][i] = sum_(site, c6) conj(F_(t,i,kind)(site, h, c6)) G(site, h, c6)[o],
+// and grad W[t][kind] = 2 (dC_0 + dC_1), grad W[t][kind + 2] = 2 (dC_0 - dC_1) (term 0: its
+// two spin factors 1 and g5 are b = 0 and 1), the sums of the CUDA-core kernel above.  As
+// real GEMMs with the sites as the reduction dimension: for each spin half h and group of
+// two terms (term 0 alone), D_h[(term, kind, i, re/im of F)][(o, re/im of G)] (M = 128,
+// N = 32) accumulates A_(h,c6) B_(h,c6)^T over c6 and over the CTA's sites, K = 32 sites
+// per tile, bf16 operands in the forward kernel's K-major core-matrix layout.  Persistent
+// CTAs (one per partial slot) keep the ten accumulators (5 groups x 2 halves, 320 TMEM
+// columns) in tensor memory for the whole launch and add them to their slot at the end.
+// Each group: 256 threads (site lane & 31, input channels 2 (tid >> 5), + 1) transport and
+// write the A tiles, one thread issues 24 tcgen05.mma, and the CTA waits (bounded) for them
+// before the tiles are overwritten.
+constexpr int TW_S = 32;                   // sites per tile
+constexpr int TW_ATILE = 128 * TW_S * 2;   // A tile: 128 rows x 32 sites, bf16
+constexpr int TW_BTILE = 32 * TW_S * 2;    // B tile: 32 rows x 32 sites
+constexpr int TW_SMEM = 12 * TW_ATILE + 12 * TW_BTILE + 8 * TW_S * 18 * 4 + 8 * TW_S * 4 + 64;
+
+__device__ __forceinline__ void tc_put_bf16(unsigned char* tile, int r, int k, float v) {
+  *(__nv_bfloat16*)(tile + tc_off(r, k)) = __float2bfloat16_rn(v);
+}
+
+// Bounded wait for the commit with the given parity; one decision for the whole CTA.
+__device__ __forceinline__ bool tc_wait_all(uint64_t* mbar, uint32_t parity) {
+  int done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"(smem_u32(mbar)), "r"(parity));
+    done = r;
+  }
+  return __syncthreads_and(done) != 0;
+}
+
+template <int G>
+__global__ void __launch_bounds__(256, 1) nn_bwdw_tc_kernel(LatDesc L, int p, FieldRef xe, FieldRef xo, FieldRef gp,
+                                                            const void* __restrict__ g32, int CI, int CO, int lgin,
+                                                            int lgout, float2* __restrict__ partial, int ntile,
+                                                            int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  unsigned char* sA = tc_smem;                      // 12 A tiles, one per (h, c6)
+  unsigned char* sB = sA + 12 * TW_ATILE;           // 12 B tiles
+  float* su = (float*)(sB + 12 * TW_BTILE);         // [8][TW_S][18] links
+  int* snb = (int*)(su + 8 * TW_S * 18);            // [8][TW_S] neighbours
+  uint64_t* mbar = (uint64_t*)(snb + 8 * TW_S);
+  uint32_t* tslot = (uint32_t*)(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, s = tid & 31;
+  const long long nin = (long long)L.Vh << lgin, nout = (long long)L.Vh << lgout;
+  const FieldRef& xs = p ? xo : xe;
+  const FieldRef& xn = p ? xe : xo;
+  const void* gb = gauge_seg<G>(g32, L);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  // M = 128, N = 32, A and B bf16 K-major, D FP32
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  bool ok = true;
+  int ncommit = 0;
+  for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
+    const int site0 = tile * TW_S, site = site0 + s;
+    const bool live = site < L.Vh;
+    __syncthreads();  // the previous tile's threads are done with su / snb
+    stage_links<G>(L, p, site0, TW_S, gb, su, snb);
+    // B tiles: the output gradient of this thread's site, outputs 2 warp and 2 warp + 1
+    for (int oo = 0; oo < 2; ++oo) {
+      const int o = 2 * warp + oo;
+      float v[24];
+      if (live && o < CO) {
+        SIO<PBF>::load(seg_ptr<PBF>(gp, L), nullptr, nout, ((long long)site << lgout) + o, v);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 24; ++m) v[m] = 0.f;
+      }
+#pragma unroll
+      for (int m = 0; m < 12; ++m) {
+        tc_put_bf16(sB + m * TW_BTILE, 2 * o, s, v[2 * m]);
+        tc_put_bf16(sB + m * TW_BTILE, 2 * o + 1, s, v[2 * m + 1]);
+      }
+    }
+    __syncthreads();  // links staged
+    for (int g = 0; g < 5 && ok; ++g) {
+      // A tiles: row ((tl * 2 + kind) * 16 + i) * 2 + re/im for term tl of the group
+      for (int tl = 0; tl < 2; ++tl) {
+        const int t = g == 0 ? (tl == 0 ? 0 : -1) : 2 * g - 1 + tl;
+        for (int ii = 0; ii < 2; ++ii) {
+          const int i = 2 * warp + ii;
+          float z[24], zg[24];
+          if (t >= 0 && live && i < CI) {
+            if (t == 0) {
+              SIO<PBF>::load(seg_ptr<PBF>(xs, L), nullptr, nin, ((long long)site << lgin) + i, z);
+#pragma unroll
+              for (int m = 0; m < 24; ++m) zg[m] = 0.f;
+            } else {
+              const int d = t - 1;
+              float v[24];
+              SIO<PBF>::load(seg_ptr<PBF>(xn, L), nullptr, nin, ((long long)snb[d * TW_S + s] << lgin) + i, v);
+              colour_mul(su + (d * TW_S + s) * 18, v, z, (d & 1) != 0);
+              gamma_apply_rt(d >> 1, z, zg);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < 24; ++m) z[m] = zg[m] = 0.f;
+          }
+          const int r0 = ((tl * 2) * 16 + i) * 2, r1 = ((tl * 2 + 1) * 16 + i) * 2;
+#pragma unroll
+          for (int m = 0; m < 12; ++m) {
+            unsigned char* a = sA + m * TW_ATILE;
+            tc_put_bf16(a, r0, s, z[2 * m]);
+            tc_put_bf16(a, r0 + 1, s, z[2 * m + 1]);
+            tc_put_bf16(a, r1, s, zg[2 * m]);
+            tc_put_bf16(a, r1 + 1, s, zg[2 * m + 1]);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const bool first_tile = tile == (int)blockIdx.x;
+#pragma unroll 1
+        for (int m = 0; m < 12; ++m)
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t da = tc_desc(smem_u32(sA + m * TW_ATILE + ks * 256));
+            const uint64_t db = tc_desc(smem_u32(sB + m * TW_BTILE + ks * 256));
+            const uint32_t acc = (first_tile && (m % 6) == 0 && ks == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(
+                    tmem + (uint32_t)((2 * g + m / 6) * 32)),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
+      }
+      // the tiles are rewritten next: wait for these MMAs (every thread, one decision)
+      if (!tc_wait_all(mbar, (uint32_t)(ncommit & 1))) {
+        ok = false;
+        if (tid == 0) atomicExch(err, 1);
+      }
+      ++ncommit;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    }
+  }
+  // an expired wait: give the MMAs in flight a second bounded wait before the release
+  if (!ok && ncommit > 0) tc_wait_all(mbar, (uint32_t)((ncommit - 1) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // epilogue: thread = accumulator row r (TMEM lane), 16 columns (8 outputs x re/im of G)
+    // of its warp's half; the partner row r ^ 1 (the other re/im of F) is the next lane
+    const int half = warp >> 2, rowbase = 32 * (warp & 3);
+    const int r = rowbase + (tid & 31);
+    const int pf = r & 1, i = (r >> 1) & 15, kind = (r >> 5) & 1, tl = (r >> 6) & 1;
+    const size_t nW = (size_t)36 * CO * CI;
+    float2* dst = partial + (size_t)blockIdx.x * nW;
+    for (int g = 0; g < 5; ++g) {
+      uint32_t d[2][16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t ta = tmem + ((uint32_t)rowbase << 16) + (uint32_t)((2 * g + h) * 32 + 16 * half);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(d[h][0]), "=r"(d[h][1]), "=r"(d[h][2]), "=r"(d[h][3]), "=r"(d[h][4]), "=r"(d[h][5]), "=r"(d[h][6]),
+              "=r"(d[h][7]), "=r"(d[h][8]), "=r"(d[h][9]), "=r"(d[h][10]), "=r"(d[h][11]), "=r"(d[h][12]),
+              "=r"(d[h][13]), "=r"(d[h][14]), "=r"(d[h][15])
+            : "r"(ta));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      const int t = g == 0 ? (tl == 0 ? 0 : -1) : 2 * g - 1 + tl;
+      const bool row_ok = pf == 0 && t >= 0 && !(t == 0 && kind == 1) && i < CI;
+      const int bs = t == 0 ? 0 : kind, bd = t == 0 ? 1 : kind + 2;
+#pragma unroll
+      for (int oo = 0; oo < 8; ++oo) {
+        float2 dc[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float ar = __uint_as_float(d[h][2 * oo]), ai = __uint_as_float(d[h][2 * oo + 1]);
+          const float br = __shfl_xor_sync(0xffffffffu, ar, 1), bi = __shfl_xor_sync(0xffffffffu, ai, 1);
+          // own row F_re, partner row F_im: conj(F) G = (F_re G_re + F_im G_im) + i (F_re G_im - F_im G_re)
+          dc[h] = make_float2(ar + bi, ai - br);
+        }
+        const int o = 8 * half + oo;
+        if (row_ok && o < CO) {
+          float2& qs = dst[((size_t)(t * 4 + bs) * CO + o) * CI + i];
+          float2& qd = dst[((size_t)(t * 4 + bd) * CO + o) * CI + i];
+          qs.x += 2.f * (dc[0].x + dc[1].x);
+          qs.y += 2.f * (dc[0].y + dc[1].y);
+          qd.x += 2.f * (dc[0].x - dc[1].x);
+          qd.y += 2.f * (dc[0].y - dc[1].y);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 }  // namespace
 
 namespace dl {
@@ -775,6 +986,29 @@ cudaError_t nn_backward_w(const LatDesc& L, int prec, int grec, int parity, Fiel
   const size_t smem = (size_t)8 * NW * 18 * 4 + 8 * NW * 4 + (size_t)2 * NW * 9 * 16 * 24 * 4 + (size_t)NW * 16 * 24 * 4;
   NN_DISPATCH(prec, grec,
               return (launch_bwdw<PP, GG>(grid, smem, L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial, ntile, st)));
+}
+
+cudaError_t nn_backward_w_tc(const LatDesc& L, int grec, int parity, FieldRef xe, FieldRef xo, FieldRef gp,
+                             const void* g32, int ci, int co, int lgin, int lgout, float2* partial, int slots, int* err,
+                             cudaStream_t st) {
+  if (ci > 16 || co > 16 || ci < 1 || co < 1 || slots < 1) return cudaErrorInvalidValue;
+  const int ntile = (L.Vh + TW_S - 1) / TW_S;
+  const int grid = slots < ntile ? slots : ntile;  // every CTA has at least one tile
+  if (grid < 1) return cudaSuccess;
+  if (grec == 12) {
+    DL_CUDA_TRY(cudaFuncSetAttribute(nn_bwdw_tc_kernel<G32R12>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    DL_COUNT();
+    nn_bwdw_tc_kernel<G32R12><<<grid, 256, TW_SMEM, st>>>(L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial,
+                                                           ntile, err);
+  } else if (grec == 8) {
+    DL_CUDA_TRY(cudaFuncSetAttribute(nn_bwdw_tc_kernel<G32R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    DL_COUNT();
+    nn_bwdw_tc_kernel<G32R8><<<grid, 256, TW_SMEM, st>>>(L, parity, xe, xo, gp, g32, ci, co, lgin, lgout, partial,
+                                                          ntile, err);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t nn_wsum(const float2* partial, int nslice, size_t nW, float2* grad, cudaStream_t st) {

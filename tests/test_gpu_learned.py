@@ -215,6 +215,44 @@ def test_loss_and_gradients_match_oracle(dl):
     assert np.abs(grad - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
+def test_tensor_core_gradients_match_oracle(dl):
+    """bfloat16 network, 16 channels, on 6x6x2x4 (4.5 tiles of 32 sites per parity): the
+    weight gradients of the tensor-core kernel (the sites as the reduction dimension of the
+    products) against the CUDA-core kernel and the oracle, layer by layer, within the
+    bfloat16 rounding of the activations; unused weight slots stay zero."""
+    dims = (6, 6, 2, 4)
+    n_layers, c = 3, 16
+    links = synth.gauge_links(dims, 0.4, 319)
+    w = synth.network_weights(n_layers, c, 69, scale=0.6, identity=0.5)
+    eta = np.stack([noise.z4_noise(dims, 17, r) for r in range(2)])
+    s = synth.gaussian_spinors(dims, 2, 70)
+    ctx = _ctx(dl, dims, links, 0.16, 0.01)
+    got = {}
+    try:
+        nn = dl.dl_nn_create(ctx, n_layers, c, dl.DL_BF16)
+        dl.dl_nn_set_weights(nn, w)
+        for tc in (1, 0):
+            dl.dl_nn_set_tensor_cores(nn, tc)
+            got[tc] = dl.dl_nn_loss_grad(nn, 2, _dev(eta), _dev(s))
+        dl.dl_nn_destroy(nn)
+    finally:
+        dl.dl_destroy(ctx)
+    ref_loss, ref_grads = network.loss_and_grads(links, _to_oracle(w, n_layers, c), list(zip(eta, s)))
+    ref = _from_oracle(ref_grads)
+    for tc in (1, 0):
+        assert abs(got[tc][0] - ref_loss) <= 3e-2 * ref_loss, tc
+    k = 0
+    for ci, co in _shapes(n_layers, c):
+        sl = slice(k, k + 36 * co * ci)
+        k += 36 * co * ci
+        sc = np.abs(ref[sl]).max()
+        assert np.abs(got[1][1][sl] - ref[sl]).max() <= 5e-2 * sc, (ci, co)
+        assert np.abs(got[1][1][sl] - got[0][1][sl]).max() <= 5e-2 * sc, (ci, co)
+        unused = np.zeros((9, 4, co, ci), dtype=bool)
+        unused[0, 2:] = True
+        assert np.all(got[1][1][sl][unused.ravel()] == 0)
+
+
 def test_residual_loss_and_gradients_match_oracle(dl):
     """The residual loss |M_u N eta - eta|^2 / |eta|^2 of three sources and every weight
     gradient, FP32 activations, against the oracle (M applied in FP32 on the GPU)."""
