@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 DIMS = (32, 32, 32, 64)
 EPS, KAPPA, AMU = 0.4, 0.1612, 0.0055
-N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 16
+N_HP, N_LP, SLICES, BLOCK = 24, 500, 1, 0  # BLOCK 0: the library's autotuner picks 8, 16 or 32
 TOL_HP, TOL_LP = 1e-10, 1e-2
 DELTA_HP = 1e-4  # reliable updates every four decades: each costs a high-precision operator application
 P2MAX = 9
@@ -237,7 +237,8 @@ def run_ours(args, rank, world, device):
     # no reliable updates; timed over a bounded number of iterations and scaled
     # by the measured HP iteration count
     dl.dl_destroy(ctx)
-    ref_batched = plain_fp64_batched(dl, device, links)
+    block = infos[-1].block  # the TSM's (tuned) block: the comparator batches the same way
+    ref_batched = plain_fp64_batched(dl, device, links, block)
     ctx = dl.dl_create(DIMS, device, stream)
     dl.dl_load_gauge(ctx, links, -1.0, 12, 12)
     dl.dl_set_params(ctx, KAPPA, AMU)
@@ -253,7 +254,7 @@ def run_ours(args, rank, world, device):
     it_hp = sum(i.iters_hp for i in infos) / max(1, len(infos) * n_hp_s)
     it_lp = sum(i.iters_lp for i in infos) / max(1, len(infos) * (n_hp_s + n_lp_s))
     return dict(value=value, t_step=t_step, wall=wall, eq=eq, roof=roof, stencils=stencils, launches=launches, ref=ref,
-                ref_batched=ref_batched, e2e=e2e_value,
+                ref_batched=ref_batched, e2e=e2e_value, block=block,
                 e2e_t=e2e_t, clocks=clk.summary(), it_hp=it_hp, it_lp=it_lp,
                 sec_hp=sum(i.seconds_hp for i in infos) / len(infos),
                 sec_lp=sum(i.seconds_lp for i in infos) / len(infos),
@@ -290,15 +291,14 @@ def plain_fp64_reference(dl, ctx, device, iters, sec_contract_per_col):
                    "scaled by the batched comparator's from-zero iteration count, plus its contraction time per column"}
 
 
-def plain_fp64_batched(dl, device, links):
-    """The plain method on this GPU with the TSM's batching: one block of BLOCK noise
+def plain_fp64_batched(dl, device, links, n):
+    """The plain method on this GPU with the TSM's batching: one block of n noise
     vectors solved from zero to 1e-10 in FP64 storage and arithmetic (no mixed precision,
     no reliable updates: every Krylov vector is FP64), timed in double-float and in IEEE
     binary64, each followed by the sweep's contractions (one-end, generalised one-end,
     HPE at |n|^2 <= 9).  Each estimate counts one at equal error.  A context of its own,
     destroyed afterwards, holds its FP64 workspaces."""
     import torch
-    n = BLOCK
     V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
     npm = len(dl.dl_momenta(P2MAX))
     per = {}
@@ -941,7 +941,9 @@ def main():
                  "f64 accumulation",
         "data": "synthetic (seeded SU(3) links exp(i eps H), eps 0.4; Z2xiZ2 noise)",
         "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA, "amu": AMU, "n_hp": N_HP, "n_lp": N_LP,
-                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "hp_from_lp": 1, "hpe_correction_from_difference": 1, "block": BLOCK, "p2max": P2MAX, "hpe_orders": 4,
+                   "tol_hp": TOL_HP, "tol_lp": TOL_LP, "delta_hp": args.delta_hp, "hp_from_lp": 1, "hpe_correction_from_difference": 1, "block": r["block"],
+                   "block_choice": "autotuned by the library (LP blocks of 8, 16, 32 timed, least time per right-hand side)"
+                   if BLOCK == 0 else "fixed", "p2max": P2MAX, "hpe_orders": 4,
                    "step": "one TSM sweep: 24 HP-LP pairs + 500 LP solves + contractions",
                    "l2": "inputs larger than L2 (gauge field 0.4-1.2 GB, spinor blocks GBs)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

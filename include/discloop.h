@@ -210,7 +210,13 @@ typedef struct {
   int prec_hp_lo;        /* Krylov storage of HP solves (FP64 accumulation, reliable updates) */
   int prec_lp_lo;        /* Krylov storage of LP solves (FP32 accumulation) */
   double delta_hp;       /* reliable-update trigger for HP solves */
-  int block;             /* right-hand sides per batched solve, <= DL_MAX_RHS */
+  int block;             /* right-hand sides per batched solve, 1..DL_MAX_RHS; 0: chosen by
+                            the autotuner: the first call on a context for a given LP
+                            precision, p2max, with_deriv, hpe and time dilution runs one LP
+                            block (noise, truncated solve, contractions) of 8, 16 and 32
+                            right-hand sides on extra noise indices (from 2^32), each once
+                            untimed and once timed, and keeps the block with the least time
+                            per right-hand side for that call and later ones (info->block) */
   uint64_t seed;         /* noise seed; HP pairs use indices 0..n_hp-1, LP n_hp.. */
   int p2max;             /* momentum cut */
   int with_deriv;        /* add the one-derivative loops */
@@ -245,7 +251,10 @@ typedef struct {
   int np, nd, n_est;     /* momenta, derivative slots, estimators (ONE_END, GEN, [HPE]) */
   double seconds_total, seconds_hp, seconds_lp, seconds_contract;
   long long iters_hp, iters_lp; /* summed over right-hand sides */
-  int not_converged;     /* right-hand sides that hit max_iter */
+  int not_converged;     /* 1 when a right-hand side hit max_iter (status DL_NOT_CONVERGED) or
+                            broke down (status DL_BREAKDOWN: the loops are not valid) */
+  int block;             /* right-hand sides per batched solve used (params->block or the tuned one) */
+  double seconds_tune;   /* spent by the autotuner in this call (0 when cached or not asked) */
 } dl_tsm_info;
 
 /* Run the TSM for one gauge field: n_hp HP/LP pairs and n_lp fresh LP solves,

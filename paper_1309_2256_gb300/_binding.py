@@ -49,7 +49,8 @@ class dl_tsm_params(C.Structure):
 class dl_tsm_info(C.Structure):
     _fields_ = [("np", C.c_int), ("nd", C.c_int), ("n_est", C.c_int), ("seconds_total", C.c_double),
                 ("seconds_hp", C.c_double), ("seconds_lp", C.c_double), ("seconds_contract", C.c_double),
-                ("iters_hp", C.c_longlong), ("iters_lp", C.c_longlong), ("not_converged", C.c_int)]
+                ("iters_hp", C.c_longlong), ("iters_lp", C.c_longlong), ("not_converged", C.c_int),
+                ("block", C.c_int), ("seconds_tune", C.c_double)]
 
 
 class dl_batch_params(C.Structure):

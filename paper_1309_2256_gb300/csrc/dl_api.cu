@@ -593,8 +593,26 @@ dl_status run_cg(dl_ctx* c, const Batch& B, const dl_solve_params& prm, Field* b
     }
     CK(cudaMemsetAsync(c->waitc, 0, DL_NCMAX * sizeof(int), c->st));
     // 16-bit search directions lose conjugacy over several decades: every reliable
-    // update restarts them from the true residual (p = r); FP32 ones are kept
-    if (lo == P16) CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), c->upd, c->st));
+    // update restarts them from the true residual (p = r).  FP32 ones are kept while the
+    // true residual agrees with the iterated one; a column that went on iterating while
+    // waiting for a batched update can take its iterated residual below the FP32 floor,
+    // and a search direction kept across a true residual more than twice as large as the
+    // iterated one (in norm) is no longer conjugate: it restarts too.
+    if (lo == P16) {
+      CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), c->upd, c->st));
+    } else if (prm.delta > 0.0) {
+      std::vector<int> dmask(n, 0);
+      bool any_drift = false;
+      for (int i = 0; i < n; ++i)
+        if (mask[i] && !(h.flags[i] & DL_FLAG_BREAKDOWN) && rr[i] > 4.0 * h.S[DL_S_RR * DL_NCMAX + i]) {
+          dmask[i] = 1;
+          any_drift = true;
+        }
+      if (any_drift) {
+        CK(cudaMemcpyAsync(c->upd, dmask.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+        CK(dl::copy(B, lo, lo, F.p->ref(), F.r->ref(), c->upd, c->st));
+      }
+    }
     {
       std::vector<int> rmask(n, 0);
       bool any_restart = false;
@@ -1356,7 +1374,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
                      double* obs_lp, dl_tsm_info* info) try {
   dl_status s;
   if ((s = check_ctx(c, true)) != DL_OK) return s;
-  if (!prm || prm->n_hp < 0 || prm->n_lp < 0 || prm->n_hp + prm->n_lp < 1 || prm->block < 1 || prm->block > DL_MAX_RHS ||
+  if (!prm || prm->n_hp < 0 || prm->n_lp < 0 || prm->n_hp + prm->n_lp < 1 || prm->block < 0 || prm->block > DL_MAX_RHS ||
       !(prm->tol_hp > 0.0) || !(prm->tol_lp > 0.0) || prm->p2max < 0 || prm->p2max > 64 || prm->max_iter < 1 ||
       prm->prec_hp_lo < DL_F64 || prm->prec_hp_lo > DL_F16 || prm->prec_lp_lo < DL_F32 || prm->prec_lp_lo > DL_F16 ||
       prm->delta_hp < 0.0 || prm->delta_hp >= 1.0)
@@ -1390,7 +1408,9 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     est_mode[1] = DL_EST_HPE;
   }
   const long long per = (long long)T * np * nd * 16;
-  const int blk = prm->block;
+  // block = 0: buffers for the largest candidate until the autotuner has chosen
+  const bool tune = prm->block == 0;
+  int blk = tune ? DL_MAX_RHS : prm->block;
   double2 *acc_d, *acc_l, *bl, *bh, *res;
   double *obs1, *obs2;
   void* p;
@@ -1426,7 +1446,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
   inf.nd = nd;
   inf.n_est = n_est;
   double t_hp = 0, t_lp = 0, t_ct = 0;
-  bool any_nc = false;
+  bool any_nc = false, any_bd = false;
 
   // one precision's pipeline: noise -> solve -> contractions into `out`
   auto run_block = [&](int n, uint64_t first, bool hp, double2* out, double* obs, dl_solve_stats* st) -> dl_status {
@@ -1463,6 +1483,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
                                         : solve_internal(c, B, sp, ee, eo, xe, po, false, st, guess);
     if (rs < 0) return rs;
     if (rs == DL_NOT_CONVERGED) any_nc = true;
+    if (rs == DL_BREAKDOWN) any_bd = true;
     CK(cudaStreamSynchronize(c->st));
     auto t1 = std::chrono::steady_clock::now();
     (hp ? t_hp : t_lp) += std::chrono::duration<double>(t1 - t0).count();
@@ -1510,6 +1531,47 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     return rs;
   };
 
+  if (tune) {
+    const std::vector<int> key{prm->prec_lp_lo, prm->p2max, prm->with_deriv, prm->hpe, prm->tdil_dt, prm->tdil_t0};
+    auto it = c->tsm_blocks.find(key);
+    if (it != c->tsm_blocks.end()) {
+      blk = it->second;
+    } else {
+      // one LP block per candidate on noise indices from 2^32 (outside any workload's),
+      // once untimed (CUDA graphs, buffers) and once timed; least time per right-hand side
+      const auto tt0 = std::chrono::steady_clock::now();
+      const double sv_hp = t_hp, sv_lp = t_lp, sv_ct = t_ct;
+      const bool sv_nc = any_nc, sv_bd = any_bd;
+      int best_b = 16;
+      double best = 1e300;
+      for (int cand : {8, 16, 32}) {
+        if (cand > DL_MAX_RHS) continue;
+        double dt = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {
+          dl_solve_stats st;
+          memset(&st, 0, sizeof(st));
+          CK(cudaStreamSynchronize(c->st));
+          const auto a0 = std::chrono::steady_clock::now();
+          if ((s = run_block(cand, (uint64_t)1 << 32, false, bl, obs1, &st)) < 0) return s;
+          CK(cudaStreamSynchronize(c->st));
+          dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - a0).count();
+        }
+        if (dt / cand < best) {
+          best = dt / cand;
+          best_b = cand;
+        }
+      }
+      t_hp = sv_hp;
+      t_lp = sv_lp;
+      t_ct = sv_ct;
+      any_nc = sv_nc;
+      any_bd = sv_bd;
+      blk = best_b;
+      c->tsm_blocks[key] = blk;
+      inf.seconds_tune = std::chrono::duration<double>(std::chrono::steady_clock::now() - tt0).count();
+    }
+  }
+  inf.block = blk;
   std::vector<double> hbuf(4 * blk);
   for (int b0 = 0; b0 < prm->n_hp; b0 += blk) {
     int n = std::min(blk, prm->n_hp - b0);
@@ -1561,10 +1623,11 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
   inf.seconds_lp = t_lp;
   inf.seconds_contract = t_ct;
   if (info) {
-    inf.not_converged = any_nc ? 1 : 0;
+    inf.not_converged = (any_nc || any_bd) ? 1 : 0;
     *info = inf;
   }
   if ((s = leave(c)) != DL_OK) return s;
+  if (any_bd) return fail(c, DL_BREAKDOWN, "a TSM solve broke down (its loops are not valid)");
   return any_nc ? fail(c, DL_NOT_CONVERGED, "a TSM solve hit max_iter") : DL_OK;
 } DL_CATCH(c)
 
@@ -1605,7 +1668,7 @@ dl_status dl_batch_loops(dl_ctx* c, const dl_batch_params* prm, double* loops, v
     sp.chunk = 0;
     dl_status rs = solve_internal(c, B, sp, ee, eo, xe, po, false, nullptr);
     if (rs < 0) return rs;
-    if (nc) *nc = rs == DL_NOT_CONVERGED;
+    if (nc) *nc = rs == DL_NOT_CONVERGED || rs == DL_BREAKDOWN;
     fe[0] = ee;
     fe[1] = eo;
     fe[2] = xe;

@@ -54,6 +54,8 @@ struct LatInfo {
 
 struct dl_ctx {
   std::vector<LatInfo> lats;  // one entry for dl_create, several for dl_create_multi
+  // TSM blocks chosen by the autotuner: (LP precision, p2max, derivative, HPE, tdil_dt, tdil_t0) -> block
+  std::map<std::vector<int>, int> tsm_blocks;
   long long Vh_total = 0;
   int dev = 0;
   cudaStream_t st = nullptr;    // internal stream (non-blocking; capturable)

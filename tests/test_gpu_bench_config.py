@@ -182,6 +182,68 @@ def test_tsm_benchmark_configuration(dl):
         assert np.abs(corr_ref).max() > 1e-4 * np.abs(ref).max()
 
 
+def test_tsm_hp_solve_from_lp_guess_after_drift(dl):
+    """HP solves started from the LP solution with FP32 Krylov vectors on a gauge field where,
+    before search directions were restarted on drift, one column's iterated residual ran far
+    below the FP32 floor while it waited for a batched reliable update, the kept direction lost
+    conjugacy and the solve diverged (reported as a breakdown the TSM ignored).  Now: status 0
+    and HP observables within 1e-8 of exact solutions (dense LU) of the same noise."""
+    dims = (8, 4, 4, 4)
+    links = synth.gauge_links(dims, 0.4, 313)
+    n_hp, n_lp, seed = 5, 1, 2313
+    npm = len(dl.dl_momenta(P2))
+    ctx = _ctx(dl, dims, links)
+    try:
+        prm = dl.dl_tsm_params(n_hp=n_hp, n_lp=n_lp, tol_hp=1e-10, tol_lp=1e-2, prec_hp_lo=dl.DL_F32,
+                               prec_lp_lo=dl.DL_F16, delta_hp=1e-4, block=BLOCK, seed=seed, p2max=P2, with_deriv=0,
+                               hpe=1, max_iter=200000, chunk=8, hp_guess=1, hpe_diff=1)
+        out = np.zeros((3, dims[3], npm, 1, 4, 4), dtype=np.complex128)
+        ohp = np.zeros((n_hp, 4))
+        st, info = dl.dl_tsm_run(ctx, prm, out, ohp, None, None)
+    finally:
+        dl.dl_destroy(ctx)
+    assert st == 0 and info.not_converged == 0
+    assert np.all(np.isfinite(out))
+    m = op.dense_matrix(links, KAPPA, AMU, 1)
+    e_exact = np.stack([noise.z4_noise(dims, seed, r) for r in range(n_hp)])
+    s_hp = np.linalg.solve(m, e_exact.reshape(n_hp, -1).T).T.reshape(e_exact.shape)
+    ref = np.stack([_observables(links, e_exact[r], s_hp[r]) for r in range(n_hp)])
+    for k in (0, 2):
+        scale = np.abs(ref[:, k]).max()
+        assert np.abs(ohp[:, k] - ref[:, k]).max() < 1e-8 * scale, k
+
+
+def test_tsm_autotuned_block(dl):
+    """block = 0: the first call times LP blocks of 8, 16 and 32 right-hand sides and keeps
+    the fastest per right-hand side; a second call reuses the choice without timing; both
+    give bit for bit the loops and observables of a call with that block given explicitly."""
+    dims = (8, 4, 4, 4)
+    links = synth.gauge_links(dims, 0.4, 313)
+    n_hp, n_lp, seed = 5, 9, 2313
+    npm = len(dl.dl_momenta(P2))
+    ctx = _ctx(dl, dims, links)
+    res = []
+    try:
+        for blk in (0, 0, None):
+            prm = dl.dl_tsm_params(n_hp=n_hp, n_lp=n_lp, tol_hp=1e-10, tol_lp=1e-2, prec_hp_lo=dl.DL_F32,
+                                   prec_lp_lo=dl.DL_F16, delta_hp=1e-4, block=res[0][1].block if blk is None else blk,
+                                   seed=seed, p2max=P2, with_deriv=0, hpe=1, max_iter=200000, chunk=32, hp_guess=1,
+                                   hpe_diff=1)
+            out = np.zeros((3, dims[3], npm, 1, 4, 4), dtype=np.complex128)
+            ohp, olp = np.zeros((n_hp, 4)), np.zeros((n_lp, 4))
+            st, info = dl.dl_tsm_run(ctx, prm, out, ohp, None, olp)
+            assert st == 0 and info.not_converged == 0
+            res.append(((out, ohp, olp), info))
+    finally:
+        dl.dl_destroy(ctx)
+    (a, ia), (b, ib), (c, ic) = res
+    assert ia.block in (8, 16, 32) and ia.seconds_tune > 0.0
+    assert ib.block == ia.block and ib.seconds_tune == 0.0
+    assert ic.block == ia.block and ic.seconds_tune == 0.0
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, z) and np.array_equal(y, z)
+
+
 def test_hp_loop_errors_per_gamma(dl):
     """The benchmark's HP map (FP32 Krylov vectors, double-float reliable updates every
     four decades, CG to 1e-10) for 12 noise vectors as one block on 4 x 4 x 4 x 8: the
