@@ -203,8 +203,10 @@ __global__ void phase_table_kernel(int X, int mx, RPair<R>* pht) {
 
 // MXT >= 0: the x-momentum extent mx is the compile-time MXT (no predicated
 // iterations in the register-blocked DFT); MXT = -1: any mx <= 8.
+// FP32 kernels with a compile-time x extent (the LP pipeline's) are compiled for three
+// resident 256-thread CTAs per SM (80 registers), the others for the default.
 template <int P, int MODE, bool DERIV, typename R, int G, int MXT>
-__global__ void __launch_bounds__(256) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
+__global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 0) ? 3 : 1) contract_x_kernel(Batch B, FieldRef s_e, FieldRef s_o, FieldRef eta_e,
                                                            FieldRef eta_o, const void* __restrict__ gbase, int mx,
                                                            int cwlog, const RPair<R>* __restrict__ phx,
                                                            RPair<R>* __restrict__ G1, Slices S) {
