@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
   const LatDesc& L = B.lat[0];
   const int lg = L.lognpad, npad = 1 << lg;
   const int cw = 1 << cwlog;                     // columns handled by this CTA
-  const int NX = 2 * mx + 1;
+  const int mxk = MXT >= 0 ? MXT : mx;           // a constant for the compile-time extents
+  const int NX = 2 * mxk + 1;
   typedef RPair<R> cr;
   cr* cs = (cr*)smem_raw;                        // [16][X][cw] site components
   cr* pht = cs + 16 * L.X * cw;                  // [NX][X] phases
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
         nq = 4;
         const int hp = cw >> 1, qlen = (L.X + 3) >> 2;
         for (int task = threadIdx.x; task < 64 * hp; task += blockDim.x) {
-          const int cp = task % hp, k = (task / hp) & 15, q = task / (16 * hp);
+          const int cp = task & (hp - 1), k = (task >> (cwlog - 1)) & 15, q = task >> (cwlog + 3);
           const int x0 = q * qlen, x1 = (x0 + qlen < L.X) ? x0 + qlen : L.X;
           float2 p0r = make_float2(0.f, 0.f), p0i = p0r, pcr[MC + 1], pci[MC + 1], qr[MC + 1], qi[MC + 1];
 #pragma unroll
@@ -348,8 +349,8 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
             p0i = add2(p0i, vi);
 #pragma unroll
             for (int m = 1; m <= MC; ++m)
-              if (MXT >= 0 || m <= mx) {
-                const cr w = pht[(mx + m) * L.X + xx];
+              if (MXT >= 0 || m <= mxk) {
+                const cr w = pht[(mxk + m) * L.X + xx];
                 const float2 c2 = dup2(w.x), s2 = dup2(w.y);
                 pcr[m] = fma2(vr, c2, pcr[m]);
                 pci[m] = fma2(vi, c2, pci[m]);
@@ -358,15 +359,15 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
               }
           }
           cr* dst = part + (size_t)(q * 16 + k) * NX * cw + 2 * cp;
-          dst[mx * cw] = cr{p0r.x, p0i.x};
-          dst[mx * cw + 1] = cr{p0r.y, p0i.y};
+          dst[mxk * cw] = cr{p0r.x, p0i.x};
+          dst[mxk * cw + 1] = cr{p0r.y, p0i.y};
 #pragma unroll
           for (int m = 1; m <= MC; ++m)
-            if (MXT >= 0 || m <= mx) {
-              dst[(mx + m) * cw] = cr{pcr[m].x - qi[m].x, pci[m].x + qr[m].x};
-              dst[(mx + m) * cw + 1] = cr{pcr[m].y - qi[m].y, pci[m].y + qr[m].y};
-              dst[(mx - m) * cw] = cr{pcr[m].x + qi[m].x, pci[m].x - qr[m].x};
-              dst[(mx - m) * cw + 1] = cr{pcr[m].y + qi[m].y, pci[m].y - qr[m].y};
+            if (MXT >= 0 || m <= mxk) {
+              dst[(mxk + m) * cw] = cr{pcr[m].x - qi[m].x, pci[m].x + qr[m].x};
+              dst[(mxk + m) * cw + 1] = cr{pcr[m].y - qi[m].y, pci[m].y + qr[m].y};
+              dst[(mxk - m) * cw] = cr{pcr[m].x + qi[m].x, pci[m].x - qr[m].x};
+              dst[(mxk - m) * cw + 1] = cr{pcr[m].y + qi[m].y, pci[m].y - qr[m].y};
             }
         }
       }
@@ -387,8 +388,8 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
           p0i += v.y;
 #pragma unroll
           for (int m = 1; m <= MC; ++m)
-            if (MXT >= 0 || m <= mx) {
-              const cr w = pht[(mx + m) * L.X + xx];
+            if (MXT >= 0 || m <= mxk) {
+              const cr w = pht[(mxk + m) * L.X + xx];
               pcr[m] += v.x * w.x;
               pci[m] += v.y * w.x;
               qr[m] += v.x * w.y;
@@ -396,12 +397,12 @@ __global__ void __launch_bounds__(256, (std::is_same<R, float>::value && MXT >= 
             }
         }
         cr* dst = part + (size_t)(q * 16 + k) * NX * cw + cc;
-        dst[mx * cw] = cr{p0r, p0i};
+        dst[mxk * cw] = cr{p0r, p0i};
 #pragma unroll
         for (int m = 1; m <= MC; ++m)
-          if (MXT >= 0 || m <= mx) {
-            dst[(mx + m) * cw] = cr{pcr[m] - qi[m], pci[m] + qr[m]};
-            dst[(mx - m) * cw] = cr{pcr[m] + qi[m], pci[m] - qr[m]};
+          if (MXT >= 0 || m <= mxk) {
+            dst[(mxk + m) * cw] = cr{pcr[m] - qi[m], pci[m] + qr[m]};
+            dst[(mxk - m) * cw] = cr{pcr[m] + qi[m], pci[m] - qr[m]};
           }
       }
     }
