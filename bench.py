@@ -5,7 +5,8 @@ Workload (32^3 x 64, eps 0.4, kappa 0.1612, a*mu 0.0055, antiperiodic in t):
 the Truncated Solver Method with N_HP = 24 high-precision (CG residual 1e-10,
 FP32 Krylov vectors, FP64 reliable updates at delta = 1e-4) and N_LP = 500 low-precision
 (residual 1e-2, 16-bit fixed-point Krylov vectors) solves of the even-odd twisted-mass
-operator, batched 16 right-hand sides per launch, each solution contracted
+operator, batched in blocks of right-hand sides whose size (8, 16 or 32) the library's
+autotuner picks (16 on this workload), each solution contracted
 into one-end (sigma loop), generalised one-end (isoscalar axial loop) and HPE
 (4 exact orders) local loops for all 16 Gamma, every t, |p|^2 <= 9.
 
@@ -15,8 +16,8 @@ on noise vectors no other step has used.
 
 value = loop estimates per second at equal statistical error: the number of
 plain high-precision loop estimates (one per noise vector) that would give the
-TSM step's error on the isoscalar axial loop (the worse of the two
-observables), per second.  Variances come from the per-noise observables of
+TSM step's error on the worse of the two observables (sigma and isoscalar axial
+loop), per second.  Variances come from the per-noise observables of
 all steps run.  The plain FP64 CG reference is reported beside it.
 """
 from __future__ import annotations
