@@ -186,6 +186,8 @@ def run_ours(args, rank, world, device):
     def step(i, record):
         ohp, opr, olp = np.zeros((n_hp_s, 4)), np.zeros((n_hp_s, 4)), np.zeros((n_lp_s, 4))
         st, info = dl.dl_tsm_run(ctx, params(i), loops, ohp, opr, olp)
+        if st != 0:  # a solve that hit max_iter or broke down: no valid loops, no valid number
+            raise RuntimeError(f"dl_tsm_run status {st}: {dl.dl_last_error(ctx)}")
         obs["hp"].append(ohp)
         obs["pair"].append(opr)
         obs["lp"].append(olp)
