@@ -252,7 +252,9 @@ typedef struct {
   double seconds_total, seconds_hp, seconds_lp, seconds_contract;
   long long iters_hp, iters_lp; /* summed over right-hand sides */
   int not_converged;     /* 1 when a right-hand side hit max_iter (status DL_NOT_CONVERGED) or
-                            broke down (status DL_BREAKDOWN: the loops are not valid) */
+                            an HP solve broke down (status DL_BREAKDOWN: the loops are not
+                            valid); an LP solve that breaks down keeps its last iterate, which
+                            Eq. estiTSM accepts as the LP map of that noise vector */
   int block;             /* right-hand sides per batched solve used (params->block or the tuned one) */
   double seconds_tune;   /* spent by the autotuner in this call (0 when cached or not asked) */
 } dl_tsm_info;

@@ -1483,7 +1483,9 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
                                         : solve_internal(c, B, sp, ee, eo, xe, po, false, st, guess);
     if (rs < 0) return rs;
     if (rs == DL_NOT_CONVERGED) any_nc = true;
-    if (rs == DL_BREAKDOWN) any_bd = true;
+    // an HP solve that broke down misses its tolerance and would bias Eq. estiTSM; an LP
+    // solve keeps its last iterate, a valid (if poorer) LP map: the estimate stays unbiased
+    if (rs == DL_BREAKDOWN && hp) any_bd = true;
     CK(cudaStreamSynchronize(c->st));
     auto t1 = std::chrono::steady_clock::now();
     (hp ? t_hp : t_lp) += std::chrono::duration<double>(t1 - t0).count();
@@ -1627,7 +1629,7 @@ dl_status dl_tsm_run(dl_ctx* c, const dl_tsm_params* prm, double* loops, double*
     *info = inf;
   }
   if ((s = leave(c)) != DL_OK) return s;
-  if (any_bd) return fail(c, DL_BREAKDOWN, "a TSM solve broke down (its loops are not valid)");
+  if (any_bd) return fail(c, DL_BREAKDOWN, "an HP solve of the TSM broke down (its loops are not valid)");
   return any_nc ? fail(c, DL_NOT_CONVERGED, "a TSM solve hit max_iter") : DL_OK;
 } DL_CATCH(c)
 
